@@ -1,0 +1,160 @@
+/*
+ * libstda — Radar-STDA on GB300 (sm_103a): C-ABI.
+ *
+ * Radar-STDA (arXiv 2307.09063) denoises the newest of three consecutive
+ * FMCW range-Doppler (RD) maps. This library runs its forward pass (Sec. IV:
+ * Eq. "concat_operation", Eqs. "mobile_encoder_stage1/2",
+ * "mobile_decoder_stage1/2", "eca_process_equation", the two skip
+ * connections of Sec. IV-D), the synthetic RD generator of Sec. III (Eqs.
+ * "discrete signal", "IF signal", "column transform", "row transform"), and
+ * the SINR metric of Sec. V-B, as CUDA kernels on the GPU.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers owned by the caller; they must
+ *    stay valid until the work queued on `stream` has finished. Host
+ *    pointers are named host_*.
+ *  - Work is queued on `stream` (NULL = the legacy default stream) and the
+ *    call returns without waiting, except stda_create, stda_destroy,
+ *    stda_get_*, stda_set_* and stda_device_status, which synchronise.
+ *  - Errors are returned as a status code; nothing aborts. The message of
+ *    the last failure of a context is in stda_last_error().
+ *  - A context is not thread-safe: calls on one context must not overlap in
+ *    host threads.
+ *  - Map layout: a window is [3][H][W] float (STDA_FP32) or bfloat16
+ *    (STDA_BF16, STDA_FP8_E4M3), frames ordered t, t-1, t-2 (channel order
+ *    of Eq. "concat_operation"); H = range bins, W = Doppler bins, both
+ *    positive multiples of 8 (the three stride-2 stages halve the map three
+ *    times). A batch is [B][3][H][W], the output [B][1][H][W] in the same
+ *    element type, values in (0, 1).
+ */
+#ifndef STDA_H
+#define STDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t */
+struct CUevent_st;  /* cudaEvent_t  */
+
+typedef struct stda_ctx stda_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  STDA_OK = 0,
+  STDA_ERR_INVALID_ARG = 1, /* null pointer, bad count, bad enum          */
+  STDA_ERR_SHAPE = 2,       /* H or W not a positive multiple of 8, B out
+                               of [0, max_batch], map larger than created */
+  STDA_ERR_OOM = 3,         /* device allocation failed                   */
+  STDA_ERR_CUDA = 4,        /* a CUDA runtime call failed                 */
+  STDA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up         */
+  STDA_ERR_BUSY = 6,        /* serving: no slot or memory free right now  */
+  STDA_ERR_UNSUPPORTED = 7, /* not available for this precision / device  */
+  STDA_WARMUP = 8           /* serving: fewer than three frames buffered  */
+} stda_status;
+
+typedef enum { STDA_FP32 = 0, STDA_BF16 = 1, STDA_FP8_E4M3 = 2 } stda_precision;
+
+typedef struct {
+  int H, W;          /* largest map size the context serves (multiples of 8) */
+  int max_batch;     /* largest batch of windows per call                    */
+  stda_precision prec;
+  uint64_t weight_seed;    /* random initialisation of the weights          */
+  size_t mem_budget_bytes; /* serving admission limit; 0 = no limit         */
+} stda_config;
+
+/* ---------------------------------------------------------------- context */
+
+/* Allocates the context, its folded weights and its activation scratch for
+ * max_batch windows of H x W, and initialises the weights from weight_seed
+ * (uniform draws of a SplitMix64 hash; see stda_get_params). Uses the
+ * current CUDA device. */
+stda_status stda_create(const stda_config* cfg, stda_ctx** out);
+stda_status stda_destroy(stda_ctx* ctx);
+
+/* 137,915: the learnable parameters in canonical order (stem; per block
+ * dw1x1, BN1, dw3x3, BN2, BN3, stage-2 weight, BN, residual weight and bias,
+ * ECA kernel; output conv weight and bias). Table "performance_radar_stda"
+ * prints 0.14 M. */
+size_t stda_num_params(void);
+/* 1,360: batch-norm running means and variances (per BN: mean[C], var[C]). */
+size_t stda_num_buffers(void);
+
+/* Host only (no GPU needed): the parameters and BN buffers that
+ * stda_create draws from `seed`. host_params[137915], host_buffers[1360]. */
+stda_status stda_init_params(uint64_t seed, float* host_params,
+                             float* host_buffers);
+
+/* Copies the FP32 parameters / BN buffers to or from host memory (n must
+ * equal the count above). stda_set_* refolds BN into the convolutions in
+ * FP64 on the host and re-uploads every precision's weights. */
+stda_status stda_get_params(stda_ctx* ctx, float* host_dst, size_t n);
+stda_status stda_set_params(stda_ctx* ctx, const float* host_src, size_t n);
+stda_status stda_get_buffers(stda_ctx* ctx, float* host_dst, size_t n);
+stda_status stda_set_buffers(stda_ctx* ctx, const float* host_src, size_t n);
+
+/* ---------------------------------------------------------------- forward */
+
+/* Denoises B windows: d_in [B][3][H][W] -> d_out [B][1][H][W] (Sec. IV-A,
+ * Eqs. "encoder_stda", "decoder_stda"). H, W may be smaller than the
+ * context's, but B*H*W may not exceed max_batch*H_ctx*W_ctx. B == 0 is a
+ * no-op. */
+stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
+                         int H, int W, struct CUstream_st* stream);
+
+/* Sticky device-side error word of the context (STDA_OK or
+ * STDA_ERR_TIMEOUT); synchronises the context's last stream. */
+stda_status stda_device_status(stda_ctx* ctx);
+const char* stda_last_error(stda_ctx* ctx);
+const char* stda_status_string(stda_status s);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Per-kernel timing: while enabled, every kernel the context launches is
+ * bracketed by a CUDA event pair recorded on the launch's own stream.
+ * Enabling or disabling synchronises the device and clears the records. */
+stda_status stda_profile(stda_ctx* ctx, int enable);
+/* Synchronises on the last record, then fills, per kernel of the forward
+ * pass (up to `max`): its name, total milliseconds and launch count since
+ * the last read, and clears the records. Returns the number of kernels, or
+ * -1 on error. Any output array may be NULL. */
+int stda_profile_read(stda_ctx* ctx, const char** names, double* total_ms,
+                      int* launches, int max);
+/* Number of kernels the context has launched since it was created. */
+uint64_t stda_launch_count(stda_ctx* ctx);
+
+/* -------------------------------------------------------------- generator */
+
+typedef struct {
+  int N, M;          /* fast-time samples per chirp, chirps per frame       */
+  int P, Q;          /* range / Doppler DFT points (P >= N, Q >= M, powers
+                        of two, P*Q <= 2^20): the map is H = P by W = Q     */
+  int tmin, tmax;    /* point targets per window, uniform integer, <= 16   */
+  int imin, imax;    /* interferers per frame, uniform integer, <= 4       */
+  double snr_min, snr_max; /* per-sample target SNR [dB]                    */
+  double inr_min, inr_max; /* interferer power above a target [dB]          */
+  double kmin, kmax;       /* interferer / victim chirp slope ratio         */
+} stda_gen_config;
+
+/* Synthesises windows w0 .. w0+B-1 of workload `cid` from `seed` (Sec. III:
+ * point targets per Eq. "discrete signal", dechirped interfering chirps and
+ * complex Gaussian noise per Eq. "IF signal", Hann window, 2-D DFT per Eqs.
+ * "column transform"/"row transform", Doppler axis centred, 20 log10
+ * magnitude min-max normalised per map), computed in FP64 on the GPU.
+ *   d_noisy  [B][3][P][Q] out, element type `bf16` ? bfloat16 : float
+ *   d_clean  [B][P][Q]    out (targets + the same noise, no interferers), or NULL
+ *   d_bins   [B][16][2]   out int32 frame-t peak cells (p*, q*), or NULL
+ *   d_ntgt   [B]          out int32 target count, or NULL
+ * Allocates temporary device memory for the duration of the call (freed in
+ * stream order). */
+stda_status stda_generate(const stda_gen_config* g, uint64_t seed,
+                          uint64_t cid, int w0, int B, int bf16,
+                          void* d_noisy, void* d_clean, int* d_bins,
+                          int* d_ntgt, struct CUstream_st* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STDA_H */

@@ -1,0 +1,554 @@
+// libstda C-ABI: context, parameters, BN folding, dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "stda_internal.h"
+
+namespace stda {
+
+// ----------------------------------------------------------------------------
+// Parameter initialisation: every value is U(lo, hi) from a SplitMix64 hash
+// of (seed, 0, 0, tag, tensor id, element), in FP64, rounded to FP32.
+// Distributions: conv / deconv weights U(+-sqrt(6 / fan)) with fan = Cin/g *
+// k^2 (conv) or Cin/g * k^2 / s^2 (transposed conv); biases U(+-0.05); BN
+// gamma U(0.8, 1.2), beta U(+-0.1), running mean U(+-0.1), running variance
+// U(0.8, 1.2); ECA kernels U(+-0.577); the output conv weights carry a gain
+// of 3 so that the sigmoid output is spread out.
+// ----------------------------------------------------------------------------
+namespace {
+
+uint64_t mix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+double u01(uint64_t seed, uint64_t tag, uint64_t i1, uint64_t i2) {
+  uint64_t h = mix64(seed);
+  h = mix64(h ^ 0);
+  h = mix64(h ^ 0);
+  h = mix64(h ^ tag);
+  h = mix64(h ^ i1);
+  h = mix64(h ^ i2);
+  return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+constexpr uint64_t TAG_WEIGHT = 20, TAG_BN_MEAN = 21, TAG_BN_VAR = 22;
+constexpr double kOutGain = 3.0;
+constexpr double kBnEps = 1e-5;
+
+struct Tensor {
+  int size;
+  double lo, hi;
+  bool out_w;
+};
+
+std::vector<Tensor> param_table() {
+  std::vector<Tensor> t;
+  auto conv = [&](int size, int fan) {
+    double b = std::sqrt(6.0 / fan);
+    t.push_back({size, -b, b, false});
+  };
+  auto bn = [&](int c) {
+    t.push_back({c, 0.8, 1.2, false});
+    t.push_back({c, -0.1, 0.1, false});
+  };
+  conv(216, 27);
+  bn(8);
+  for (int b = 0; b < kNumBlocks; ++b) {
+    int ci = kBlkCin[b], co = kBlkCout[b];
+    conv(ci, 1);
+    bn(ci);
+    conv(9 * ci, 9);
+    bn(ci);
+    bn(ci);
+    int dense = kBlkEnc[b] ? co * ci * 9 : ci * co * 16;
+    int fan = kBlkEnc[b] ? ci * 9 : ci * 16 / 4;
+    conv(dense, fan);
+    bn(co);
+    conv(dense, fan);
+    t.push_back({co, -0.05, 0.05, false});
+    t.push_back({3, -0.577, 0.577, false});
+  }
+  conv(72, 72);
+  t.back().out_w = true;
+  t.push_back({1, -0.05, 0.05, false});
+  return t;
+}
+
+std::vector<int> bn_channels() {
+  std::vector<int> c{8};
+  for (int b = 0; b < kNumBlocks; ++b) {
+    c.push_back(kBlkCin[b]);
+    c.push_back(kBlkCin[b]);
+    c.push_back(kBlkCin[b]);
+    c.push_back(kBlkCout[b]);
+  }
+  return c;
+}
+
+}  // namespace
+
+void init_params(uint64_t seed, float* params, float* buffers) {
+  auto tab = param_table();
+  size_t off = 0;
+  for (size_t tid = 0; tid < tab.size(); ++tid) {
+    const Tensor& t = tab[tid];
+    for (int i = 0; i < t.size; ++i) {
+      double u = u01(seed, TAG_WEIGHT, tid, (uint64_t)i);
+      double v = t.lo + (t.hi - t.lo) * u;
+      if (t.out_w) v = v * kOutGain;
+      params[off++] = (float)v;
+    }
+  }
+  auto ch = bn_channels();
+  size_t q = 0;
+  for (size_t bid = 0; bid < ch.size(); ++bid) {
+    for (int i = 0; i < ch[bid]; ++i) buffers[q + i] = (float)(-0.1 + 0.2 * u01(seed, TAG_BN_MEAN, bid, i));
+    for (int i = 0; i < ch[bid]; ++i)
+      buffers[q + ch[bid] + i] = (float)(0.8 + 0.4 * u01(seed, TAG_BN_VAR, bid, i));
+    q += 2 * ch[bid];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// BN folding (inference form): BN(y) = s * y + t, s = gamma / sqrt(var + eps),
+// t = beta - mean * s. Stage 1 of a block is BN1(dw1x1 x) + BN2(dw3x3 x) +
+// BN3(x): one depthwise 3x3 cross-correlation whose centre tap gathers
+// s1 * w1 + s3, bias t1 + t2 + t3. The decoder's stride-1 transposed 3x3 is
+// the cross-correlation with the kernel flipped in both axes.
+// ----------------------------------------------------------------------------
+FoldedOffsets folded_layout() {
+  FoldedOffsets o;
+  size_t p = 0;
+  auto take = [&](size_t n) {
+    size_t r = p;
+    p += (n + 63) / 64 * 64;
+    return r;
+  };
+  o.stem_w = take(27 * 8);
+  o.stem_b = take(8);
+  for (int b = 0; b < kNumBlocks; ++b) {
+    int ci = kBlkCin[b], co = kBlkCout[b];
+    size_t dense = (size_t)(kBlkEnc[b] ? 9 : 16) * ci * co;
+    o.dw[b] = take(9 * ci);
+    o.dwb[b] = take(ci);
+    o.w2[b] = take(dense);
+    o.b2[b] = take(co);
+    o.rw[b] = take(dense);
+    o.rb[b] = take(co);
+    o.eca[b] = take(3);
+  }
+  o.out_w = take(72);
+  o.out_b = take(1);
+  o.total = p;
+  return o;
+}
+
+namespace {
+struct Cursor {
+  const float* p;
+  std::vector<double> take(int n) {
+    std::vector<double> v(p, p + n);
+    p += n;
+    return v;
+  }
+};
+struct BnFold {
+  std::vector<double> s, t;
+};
+BnFold bn_fold(const std::vector<double>& g, const std::vector<double>& be, const float*& buf, int c) {
+  BnFold r;
+  r.s.resize(c);
+  r.t.resize(c);
+  for (int i = 0; i < c; ++i) {
+    double mean = buf[i], var = buf[c + i];
+    r.s[i] = g[i] / std::sqrt(var + kBnEps);
+    r.t[i] = be[i] - mean * r.s[i];
+  }
+  buf += 2 * c;
+  return r;
+}
+}  // namespace
+
+void fold_params(const float* params, const float* buffers, float* dst, FoldedOffsets* off) {
+  *off = folded_layout();
+  std::memset(dst, 0, sizeof(float) * off->total);
+  Cursor c{params};
+  const float* bq = buffers;
+  {
+    auto w = c.take(216);
+    auto g = c.take(8);
+    auto be = c.take(8);
+    BnFold f = bn_fold(g, be, bq, 8);
+    for (int o = 0; o < 8; ++o)
+      for (int ci = 0; ci < 3; ++ci)
+        for (int t = 0; t < 9; ++t) dst[off->stem_w + (ci * 9 + t) * 8 + o] = (float)(w[(o * 3 + ci) * 9 + t] * f.s[o]);
+    for (int o = 0; o < 8; ++o) dst[off->stem_b + o] = (float)f.t[o];
+  }
+  for (int b = 0; b < kNumBlocks; ++b) {
+    int ci = kBlkCin[b], co = kBlkCout[b];
+    bool enc = kBlkEnc[b];
+    int dense = enc ? co * ci * 9 : ci * co * 16;
+    auto w1 = c.take(ci);
+    auto g1 = c.take(ci), b1 = c.take(ci);
+    auto w3 = c.take(9 * ci);
+    auto g2 = c.take(ci), b2 = c.take(ci);
+    auto g3 = c.take(ci), b3 = c.take(ci);
+    auto w2 = c.take(dense);
+    auto g = c.take(co), be = c.take(co);
+    auto rw = c.take(dense);
+    auto rb = c.take(co);
+    auto eca = c.take(3);
+    BnFold f1 = bn_fold(g1, b1, bq, ci), f2 = bn_fold(g2, b2, bq, ci), f3 = bn_fold(g3, b3, bq, ci);
+    BnFold fm = bn_fold(g, be, bq, co);
+    for (int ch = 0; ch < ci; ++ch) {
+      for (int t = 0; t < 9; ++t) {
+        double k = f2.s[ch] * w3[ch * 9 + (enc ? t : 8 - t)];
+        if (t == 4) k += f1.s[ch] * w1[ch] + f3.s[ch];
+        dst[off->dw[b] + t * ci + ch] = (float)k;
+      }
+      dst[off->dwb[b] + ch] = (float)(f1.t[ch] + f2.t[ch] + f3.t[ch]);
+    }
+    if (enc) {
+      for (int o = 0; o < co; ++o)
+        for (int i = 0; i < ci; ++i)
+          for (int t = 0; t < 9; ++t) {
+            size_t d = ((size_t)t * ci + i) * co + o;
+            dst[off->w2[b] + d] = (float)(w2[((size_t)o * ci + i) * 9 + t] * fm.s[o]);
+            dst[off->rw[b] + d] = (float)rw[((size_t)o * ci + i) * 9 + t];
+          }
+    } else {
+      for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px)
+          for (int sy = 0; sy < 2; ++sy)
+            for (int sx = 0; sx < 2; ++sx) {
+              int dy = sy - 1 + py, dx = sx - 1 + px;
+              int ky = py + 1 - 2 * dy, kx = px + 1 - 2 * dx;
+              int ph = py * 2 + px, st = sy * 2 + sx;
+              for (int i = 0; i < ci; ++i)
+                for (int o = 0; o < co; ++o) {
+                  size_t s = (((size_t)i * co + o) * 4 + ky) * 4 + kx;
+                  size_t d = (((size_t)ph * 4 + st) * ci + i) * co + o;
+                  dst[off->w2[b] + d] = (float)(w2[s] * fm.s[o]);
+                  dst[off->rw[b] + d] = (float)rw[s];
+                }
+            }
+    }
+    for (int o = 0; o < co; ++o) {
+      dst[off->b2[b] + o] = (float)fm.t[o];
+      dst[off->rb[b] + o] = (float)rb[o];
+    }
+    for (int j = 0; j < 3; ++j) dst[off->eca[b] + j] = (float)eca[j];
+  }
+  auto ow = c.take(72);
+  auto ob = c.take(1);
+  for (int ch = 0; ch < 8; ++ch)
+    for (int t = 0; t < 9; ++t) dst[off->out_w + t * 8 + ch] = (float)ow[ch * 9 + t];
+  dst[off->out_b] = (float)ob[0];
+}
+
+const char* const kKernelNames[K_NUM_IDS] = {"enc1_stem", "enc2", "enc3", "dec1", "dec2", "dec3", "out"};
+
+NetW net_from(const float* base, const FoldedOffsets& o) {
+  NetW n;
+  n.stem_w = base + o.stem_w;
+  n.stem_b = base + o.stem_b;
+  for (int b = 0; b < kNumBlocks; ++b)
+    n.blk[b] = BlockW{base + o.dw[b], base + o.dwb[b], base + o.w2[b], base + o.b2[b],
+                      base + o.rw[b], base + o.rb[b], base + o.eca[b]};
+  n.out_w = base + o.out_w;
+  n.out_b = base + o.out_b;
+  return n;
+}
+
+}  // namespace stda
+
+// ============================================================================
+// C-ABI
+// ============================================================================
+namespace {
+// Counts launches; when enabled, records a CUDA event pair around every
+// launch on the launch's own stream.
+struct Profiler : stda::KernelHook {
+  bool on = false;
+  uint64_t launches = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  int cur_id = 0;
+  cudaEvent_t cur = nullptr;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int id, cudaStream_t st) override {
+    ++launches;
+    if (!on) return;
+    cur_id = id;
+    cur = next();
+    cudaEventRecord(cur, st);
+  }
+  void end(cudaStream_t st) override {
+    if (!on) return;
+    cudaEvent_t e = next();
+    cudaEventRecord(e, st);
+    recs.push_back({cur_id, cur, e});
+  }
+  void reset() {
+    recs.clear();
+    used = 0;
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
+struct stda_ctx {
+  Profiler prof;
+  stda_config cfg;
+  int device = 0;
+  std::vector<float> params, buffers;
+  stda::FoldedOffsets off;
+  float* d_folded = nullptr;
+  stda::NetW net;
+  void* d_scratch = nullptr;
+  size_t scratch_size = 0;
+  int* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace {
+
+stda_status fail(stda_ctx* c, stda_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+stda_status cuda_fail(stda_ctx* c, cudaError_t e, const char* where) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? STDA_ERR_OOM : STDA_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t elem_size(stda_precision p) { return p == STDA_FP32 ? 4 : 2; }
+
+stda_status upload_weights(stda_ctx* c) {
+  std::vector<float> host(stda::folded_layout().total);
+  stda::fold_params(c->params.data(), c->buffers.data(), host.data(), &c->off);
+  cudaError_t e = cudaMemcpy(c->d_folded, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e) return cuda_fail(c, e, "upload weights");
+  c->net = stda::net_from(c->d_folded, c->off);
+  return STDA_OK;
+}
+
+bool shape_ok(int H, int W) { return H > 0 && W > 0 && H % 8 == 0 && W % 8 == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* stda_status_string(stda_status s) {
+  switch (s) {
+    case STDA_OK: return "ok";
+    case STDA_ERR_INVALID_ARG: return "invalid argument";
+    case STDA_ERR_SHAPE: return "invalid shape";
+    case STDA_ERR_OOM: return "out of device memory";
+    case STDA_ERR_CUDA: return "CUDA error";
+    case STDA_ERR_TIMEOUT: return "device wait timed out";
+    case STDA_ERR_BUSY: return "busy";
+    case STDA_ERR_UNSUPPORTED: return "unsupported";
+    case STDA_WARMUP: return "warming up (fewer than three frames)";
+  }
+  return "unknown status";
+}
+
+size_t stda_num_params(void) { return stda::kNumParams; }
+size_t stda_num_buffers(void) { return stda::kNumBuffers; }
+
+stda_status stda_create(const stda_config* cfg, stda_ctx** out) {
+  if (!cfg || !out) return STDA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!shape_ok(cfg->H, cfg->W) || cfg->max_batch < 1) return STDA_ERR_SHAPE;
+  if (cfg->prec != STDA_FP32 && cfg->prec != STDA_BF16 && cfg->prec != STDA_FP8_E4M3)
+    return STDA_ERR_INVALID_ARG;
+  stda_ctx* c = new stda_ctx;
+  c->cfg = *cfg;
+  cudaGetDevice(&c->device);
+  c->params.resize(stda::kNumParams);
+  c->buffers.resize(stda::kNumBuffers);
+  stda::init_params(cfg->weight_seed, c->params.data(), c->buffers.data());
+  if (cudaMalloc((void**)&c->d_folded, stda::folded_layout().total * sizeof(float))) {
+    cudaGetLastError();
+    stda_destroy(c);
+    return STDA_ERR_OOM;
+  }
+  c->scratch_size = stda::scratch_bytes(cfg->max_batch, cfg->H, cfg->W, elem_size(cfg->prec));
+  if (cudaMalloc(&c->d_scratch, c->scratch_size)) {
+    cudaGetLastError();
+    stda_destroy(c);
+    return STDA_ERR_OOM;
+  }
+  if (cudaMalloc((void**)&c->d_status, sizeof(int)) || cudaMemset(c->d_status, 0, sizeof(int))) {
+    cudaGetLastError();
+    stda_destroy(c);
+    return STDA_ERR_OOM;
+  }
+  stda_status s = upload_weights(c);
+  if (s != STDA_OK) {
+    stda_destroy(c);
+    return s;
+  }
+  *out = c;
+  return STDA_OK;
+}
+
+stda_status stda_destroy(stda_ctx* c) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  if (c->d_folded) cudaFree(c->d_folded);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+  return STDA_OK;
+}
+
+stda_status stda_init_params(uint64_t seed, float* params, float* buffers) {
+  if (!params || !buffers) return STDA_ERR_INVALID_ARG;
+  stda::init_params(seed, params, buffers);
+  return STDA_OK;
+}
+
+stda_status stda_get_params(stda_ctx* c, float* dst, size_t n) {
+  if (!c || !dst || n != c->params.size()) return fail(c, STDA_ERR_INVALID_ARG, "get_params: bad arguments");
+  std::memcpy(dst, c->params.data(), n * sizeof(float));
+  return STDA_OK;
+}
+
+stda_status stda_set_params(stda_ctx* c, const float* src, size_t n) {
+  if (!c || !src || n != c->params.size()) return fail(c, STDA_ERR_INVALID_ARG, "set_params: bad arguments");
+  cudaDeviceSynchronize();
+  std::memcpy(c->params.data(), src, n * sizeof(float));
+  return upload_weights(c);
+}
+
+stda_status stda_get_buffers(stda_ctx* c, float* dst, size_t n) {
+  if (!c || !dst || n != c->buffers.size()) return fail(c, STDA_ERR_INVALID_ARG, "get_buffers: bad arguments");
+  std::memcpy(dst, c->buffers.data(), n * sizeof(float));
+  return STDA_OK;
+}
+
+stda_status stda_set_buffers(stda_ctx* c, const float* src, size_t n) {
+  if (!c || !src || n != c->buffers.size()) return fail(c, STDA_ERR_INVALID_ARG, "set_buffers: bad arguments");
+  cudaDeviceSynchronize();
+  std::memcpy(c->buffers.data(), src, n * sizeof(float));
+  return upload_weights(c);
+}
+
+stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int H, int W, cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (B < 0 || B > c->cfg.max_batch) return fail(c, STDA_ERR_SHAPE, "forward: batch out of range");
+  if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "forward: H and W must be positive multiples of 8");
+  if (B == 0) return STDA_OK;
+  if (!d_in || !d_out) return fail(c, STDA_ERR_INVALID_ARG, "forward: null pointer");
+  size_t es = elem_size(c->cfg.prec);
+  if (stda::scratch_bytes(B, H, W, es) > c->scratch_size)
+    return fail(c, STDA_ERR_SHAPE, "forward: B*H*W exceeds the context's scratch");
+  stda::FwdScratch s;
+  stda::scratch_carve(c->d_scratch, B, H, W, es, &s);
+  c->last_stream = st;
+  cudaError_t e;
+  switch (c->cfg.prec) {
+    case STDA_FP32:
+      e = stda::forward_simt<float>(c->net, (const float*)d_in, (float*)d_out, B, H, W, s, st, &c->prof);
+      break;
+    case STDA_BF16:
+      e = stda::forward_simt<__nv_bfloat16>(c->net, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W,
+                                            s, st, &c->prof);
+      break;
+    default:
+      return fail(c, STDA_ERR_UNSUPPORTED, "forward: precision not built yet");
+  }
+  if (e) return cuda_fail(c, e, "forward");
+  return STDA_OK;
+}
+
+stda_status stda_device_status(stda_ctx* c) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  int h = 0;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e) return cuda_fail(c, e, "device_status");
+  e = cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(c, e, "device_status");
+  return (stda_status)h;
+}
+
+const char* stda_last_error(stda_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+stda_status stda_profile(stda_ctx* c, int enable) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  c->prof.on = enable != 0;
+  c->prof.reset();
+  return STDA_OK;
+}
+
+int stda_profile_read(stda_ctx* c, const char** names, double* total_ms, int* launches, int max) {
+  if (!c || max < 0) return -1;
+  int n = stda::K_NUM_IDS < max ? stda::K_NUM_IDS : max;
+  std::vector<double> t(stda::K_NUM_IDS, 0.0);
+  std::vector<int> k(stda::K_NUM_IDS, 0);
+  if (!c->prof.recs.empty() && cudaEventSynchronize(c->prof.recs.back().b)) {
+    cudaGetLastError();
+    return -1;
+  }
+  for (auto& r : c->prof.recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    t[r.id] += ms;
+    k[r.id] += 1;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (names) names[i] = stda::kKernelNames[i];
+    if (total_ms) total_ms[i] = t[i];
+    if (launches) launches[i] = k[i];
+  }
+  c->prof.reset();
+  return n;
+}
+
+uint64_t stda_launch_count(stda_ctx* c) { return c ? c->prof.launches : 0; }
+
+stda_status stda_generate(const stda_gen_config* g, uint64_t seed, uint64_t cid, int w0, int B, int bf16,
+                          void* d_noisy, void* d_clean, int* d_bins, int* d_ntgt, cudaStream_t st) {
+  if (!g || B < 0 || w0 < 0) return STDA_ERR_INVALID_ARG;
+  if (B == 0) return STDA_OK;
+  if (!d_noisy) return STDA_ERR_INVALID_ARG;
+  auto pow2 = [](int v) { return v >= 8 && v <= 1024 && (v & (v - 1)) == 0; };
+  if (!pow2(g->P) || !pow2(g->Q) || g->N < 4 || g->M < 2 || g->N > g->P || g->M > g->Q) return STDA_ERR_SHAPE;
+  if (g->tmin < 0 || g->tmax < g->tmin || g->tmax > 16 || g->imin < 0 || g->imax < g->imin || g->imax > 4)
+    return STDA_ERR_INVALID_ARG;
+  cudaError_t e = stda::generate(g, seed, cid, w0, B, bf16, d_noisy, d_clean, d_bins, d_ntgt, st);
+  if (e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? STDA_ERR_OOM : STDA_ERR_CUDA;
+  }
+  return STDA_OK;
+}
+
+}  // extern "C"

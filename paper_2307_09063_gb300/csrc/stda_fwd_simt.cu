@@ -1,0 +1,499 @@
+// Radar-STDA forward pass on the CUDA cores (FP32 arithmetic).
+//
+// One kernel per network level, each over 2-D output tiles of one window:
+//   E1 = stem + encoder block 1, E2, E3, D1, D2, D3, then the output conv.
+// A kernel stages its input tile plus halo in shared memory, applying the
+// ECA channel weights of the producing block on load (Eq.
+// "eca_process_equation") and the skip addition of Sec. IV-D, recomputes
+// stage 1 (Eqs. mobile_*_stage1, folded to one depthwise 3x3 + bias + ReLU)
+// on the tile, runs stage 2 (Eqs. mobile_*_stage2) and stores the block's
+// pre-ECA output in NHWC. ECA needs the global average of each output
+// channel over the whole map, so every tile writes its own channel sums
+// (fixed-order reduction, deterministic) and the consumer kernel reduces
+// them before it loads its input.
+#include <cuda_bf16.h>
+
+#include "stda_internal.h"
+
+namespace stda {
+namespace {
+
+__device__ __forceinline__ float tof(float v) { return v; }
+__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T>
+__device__ __forceinline__ T fromf(float v);
+template <>
+__device__ __forceinline__ float fromf<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 fromf<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+constexpr int kThreads = 256;
+
+// ECA weights of one window from the per-tile channel sums of the block that
+// produced the map: g = GAP (mean), z = 1-D conv (k = 3, zero padding),
+// s = sigmoid(z).
+__device__ void eca_scales(const float* __restrict__ part, int ntiles, int C,
+                           float inv_n, const float* __restrict__ k3,
+                           float* s_g, float* s_s) {
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float a = 0.f;
+    for (int t = 0; t < ntiles; ++t) a += part[t * C + c];
+    s_g[c] = a * inv_n;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float z = k3[1] * s_g[c];
+    if (c > 0) z += k3[0] * s_g[c - 1];
+    if (c + 1 < C) z += k3[2] * s_g[c + 1];
+    s_s[c] = 1.f / (1.f + expf(-z));
+  }
+  __syncthreads();
+}
+
+// Per-channel sums of a tile [npix][C] held in shared memory; one warp per
+// channel, fixed summation order.
+__device__ void tile_sums(const float* tile, int npix, int C, float* __restrict__ out) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < C; c += nw) {
+    float a = 0.f;
+    for (int p = lane; p < npix; p += 32) a += tile[p * C + c];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[c] = a;
+  }
+}
+
+template <typename T>
+struct EncArgs {
+  const T* in;          // STEM: [B][3][H][W]; else previous block [B][H][W][CI]
+  const float* ppart;   // previous block's tile sums [B][ptiles][CI]
+  const float* pk3;     // previous block's ECA kernel
+  int ptiles;
+  int H, W;             // input map of this block
+  NetW w;
+  int blk;
+  T* out;               // [B][H/2][W/2][2 CI]
+  float* part;          // [B][tiles][2 CI]
+};
+
+template <int CI, int TY, int TX, bool STEM>
+struct EncSmem {
+  static constexpr int CIP = CI + 1;  // padded pixel stride (bank spread)
+  static constexpr int R0 = 2 * TY + 3, C0 = 2 * TX + 3;
+  static constexpr int R1 = 2 * TY + 1, C1 = 2 * TX + 1;
+  static constexpr int RI = R0 + 2, CIW = C0 + 2;
+  static constexpr int CO = 2 * CI;
+  static constexpr int n_in = STEM ? 3 * RI * CIW : 0;
+  static constexpr int n_x0 = R0 * C0 * CIP;
+  static constexpr int n_x1 = R1 * C1 * CIP;
+  static constexpr int n_o = TY * TX * CO;
+  static constexpr int n_eca = 2 * 64;
+  static constexpr size_t bytes = sizeof(float) * (n_in + n_x0 + n_x1 + n_o + n_eca);
+};
+
+// Encoder block (stem fused in front of block 1): output tile TY x TX at
+// half resolution. Rows/cols of the staged regions:
+//   x1 (stage-1 output) from 2*oy0 - 1, size 2 TY + 1;
+//   x0 (block input)    from 2*oy0 - 2, size 2 TY + 3;
+//   raw maps (stem)     from 2*oy0 - 3, size 2 TY + 5.
+template <typename T, int CI, int TY, int TX, bool STEM>
+__global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
+  using S = EncSmem<CI, TY, TX, STEM>;
+  constexpr int CIP = S::CIP, CO = S::CO;
+  extern __shared__ float sm[];
+  float* s_in = sm;
+  float* s_x0 = s_in + S::n_in;
+  float* s_x1 = s_x0 + S::n_x0;
+  float* s_o = s_x1 + S::n_x1;
+  float* s_g = s_o + S::n_o;
+  float* s_s = s_g + 64;
+  const int b = blockIdx.z, H = a.H, W = a.W, ho = H / 2, wo = W / 2;
+  const int oy0 = blockIdx.y * TY, ox0 = blockIdx.x * TX;
+  const int y0 = 2 * oy0 - 2, x0c = 2 * ox0 - 2;
+  const BlockW bw = a.w.blk[a.blk];
+
+  if (STEM) {
+    const T* in = a.in + (size_t)b * 3 * H * W;
+    for (int i = threadIdx.x; i < S::n_in; i += blockDim.x) {
+      int c = i / (S::RI * S::CIW), r = (i / S::CIW) % S::RI, q = i % S::CIW;
+      int y = y0 - 1 + r, x = x0c - 1 + q;
+      s_in[i] = (y >= 0 && y < H && x >= 0 && x < W) ? tof(in[((size_t)c * H + y) * W + x]) : 0.f;
+    }
+    __syncthreads();
+    // stem: conv3x3 3 -> 8 (BN folded) + ReLU; zero outside the map (padding)
+    for (int i = threadIdx.x; i < S::R0 * S::C0; i += blockDim.x) {
+      int r = i / S::C0, q = i % S::C0, y = y0 + r, x = x0c + q;
+      float acc[8];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) acc[o] = a.w.stem_b[o];
+      bool inside = (y >= 0 && y < H && x >= 0 && x < W);
+      if (inside) {
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            float v = s_in[(c * S::RI + r + t / 3) * S::CIW + q + t % 3];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) acc[o] += v * a.w.stem_w[(c * 9 + t) * 8 + o];
+          }
+      }
+#pragma unroll
+      for (int o = 0; o < 8; ++o) s_x0[i * CIP + o] = inside ? fmaxf(acc[o], 0.f) : 0.f;
+    }
+  } else {
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(H * W), a.pk3, s_g, s_s);
+    const T* in = a.in + (size_t)b * H * W * CI;
+    for (int i = threadIdx.x; i < S::R0 * S::C0 * CI; i += blockDim.x) {
+      int c = i % CI, p = i / CI, r = p / S::C0, q = p % S::C0, y = y0 + r, x = x0c + q;
+      s_x0[p * CIP + c] =
+          (y >= 0 && y < H && x >= 0 && x < W) ? s_s[c] * tof(in[((size_t)y * W + x) * CI + c]) : 0.f;
+    }
+  }
+  __syncthreads();
+  // stage 1 (folded depthwise 3x3 + bias + ReLU), zero outside the map
+  for (int i = threadIdx.x; i < S::R1 * S::C1 * CI; i += blockDim.x) {
+    int c = i % CI, p = i / CI, r = p / S::C1, q = p % S::C1, y = y0 + 1 + r, x = x0c + 1 + q;
+    float v = 0.f;
+    if (y >= 0 && y < H && x >= 0 && x < W) {
+      v = bw.dwb[c];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) v += bw.dw[t * CI + c] * s_x0[((r + t / 3) * S::C0 + q + t % 3) * CIP + c];
+      v = fmaxf(v, 0.f);
+    }
+    s_x1[p * CIP + c] = v;
+  }
+  __syncthreads();
+  // stage 2: ReLU(BN(conv3x3-s2 x1)) + conv3x3-s2(x0) + bias
+  constexpr int NPIX = TY * TX, NG = CO / 8;
+  for (int it = threadIdx.x; it < NPIX * NG; it += blockDim.x) {
+    int g = it / NPIX, p = it % NPIX, ty = p / TX, tx = p % TX;
+    float am[8], ar[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      am[o] = bw.b2[g * 8 + o];
+      ar[o] = bw.rb[g * 8 + o];
+    }
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      int ky = t / 3, kx = t % 3;
+      const float* v1 = s_x1 + ((2 * ty + ky) * S::C1 + 2 * tx + kx) * CIP;
+      const float* v0 = s_x0 + ((2 * ty + ky + 1) * S::C0 + 2 * tx + kx + 1) * CIP;
+      const float4* wm = reinterpret_cast<const float4*>(bw.w2 + (size_t)t * CI * CO + g * 8);
+      const float4* wr = reinterpret_cast<const float4*>(bw.rw + (size_t)t * CI * CO + g * 8);
+#pragma unroll 4
+      for (int ci = 0; ci < CI; ++ci) {
+        float x1v = v1[ci], x0v = v0[ci];
+        float4 m0 = __ldg(wm + ci * (CO / 4)), m1 = __ldg(wm + ci * (CO / 4) + 1);
+        float4 r0 = __ldg(wr + ci * (CO / 4)), r1 = __ldg(wr + ci * (CO / 4) + 1);
+        am[0] += x1v * m0.x; am[1] += x1v * m0.y; am[2] += x1v * m0.z; am[3] += x1v * m0.w;
+        am[4] += x1v * m1.x; am[5] += x1v * m1.y; am[6] += x1v * m1.z; am[7] += x1v * m1.w;
+        ar[0] += x0v * r0.x; ar[1] += x0v * r0.y; ar[2] += x0v * r0.z; ar[3] += x0v * r0.w;
+        ar[4] += x0v * r1.x; ar[5] += x0v * r1.y; ar[6] += x0v * r1.z; ar[7] += x0v * r1.w;
+      }
+    }
+    int oy = oy0 + ty, ox = ox0 + tx;
+    bool valid = oy < ho && ox < wo;
+    T* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO + g * 8;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      float v = fmaxf(am[o], 0.f) + ar[o];
+      s_o[p * CO + g * 8 + o] = valid ? v : 0.f;
+      if (valid) dst[o] = fromf<T>(v);
+    }
+  }
+  __syncthreads();
+  int tiles = gridDim.x * gridDim.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
+  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO);
+}
+
+template <typename T>
+struct DecArgs {
+  const T* A;           // block input (previous block's pre-ECA output) [B][h][w][CI]
+  const float* Apart;
+  const float* Ak3;
+  int Atiles;
+  const T* S;           // skip operand [B][h][w][CI] or null
+  const float* Spart;
+  const float* Sk3;
+  int Stiles;
+  int h, w;             // input map of this block
+  NetW wt;
+  int blk;
+  T* out;               // [B][2h][2w][CI/2]
+  float* part;
+};
+
+template <int CI, int TY, int TX>
+struct DecSmem {
+  static constexpr int CIP = CI + 1;
+  static constexpr int R0 = TY / 2 + 4, C0 = TX / 2 + 4;
+  static constexpr int R1 = TY / 2 + 2, C1 = TX / 2 + 2;
+  static constexpr int CO = CI / 2;
+  static constexpr int n_x0 = R0 * C0 * CIP;
+  static constexpr int n_x1 = R1 * C1 * CIP;
+  static constexpr int n_o = TY * TX * CO;
+  static constexpr int n_eca = 4 * 64;
+  static constexpr size_t bytes = sizeof(float) * (n_x0 + n_x1 + n_o + n_eca);
+};
+
+// Decoder block: output tile TY x TX (both even) at double resolution. The
+// stride-2 4x4 transposed convolution (pad 1) in sub-pixel form: output
+// (2a + py, 2b + px) sums input (a + dy, b + dx) with dy in {-1, 0} (py = 0)
+// or {0, 1} (py = 1), kernel row py + 1 - 2 dy (same for columns).
+//   x1 (stage-1 output) from Y0/2 - 1, size TY/2 + 2;
+//   x0 (block input)    from Y0/2 - 2, size TY/2 + 4.
+template <typename T, int CI, int TY, int TX, bool SKIP>
+__global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
+  using S = DecSmem<CI, TY, TX>;
+  constexpr int CIP = S::CIP, CO = S::CO;
+  extern __shared__ float sm[];
+  float* s_x0 = sm;
+  float* s_x1 = s_x0 + S::n_x0;
+  float* s_o = s_x1 + S::n_x1;
+  float* s_g = s_o + S::n_o;
+  float* s_sa = s_g + 64;
+  float* s_ss = s_sa + 64;
+  const int b = blockIdx.z, h = a.h, w = a.w, Ho = 2 * h, Wo = 2 * w;
+  const int Y0 = blockIdx.y * TY, X0 = blockIdx.x * TX;
+  const int y0 = Y0 / 2 - 2, x0c = X0 / 2 - 2;
+  const BlockW bw = a.wt.blk[a.blk];
+  const float inv_n = 1.f / (float)(h * w);
+  eca_scales(a.Apart + (size_t)b * a.Atiles * CI, a.Atiles, CI, inv_n, a.Ak3, s_g, s_sa);
+  if (SKIP) eca_scales(a.Spart + (size_t)b * a.Stiles * CI, a.Stiles, CI, inv_n, a.Sk3, s_g, s_ss);
+  const T* A = a.A + (size_t)b * h * w * CI;
+  const T* Sk = SKIP ? a.S + (size_t)b * h * w * CI : nullptr;
+  for (int i = threadIdx.x; i < S::R0 * S::C0 * CI; i += blockDim.x) {
+    int c = i % CI, p = i / CI, r = p / S::C0, q = p % S::C0, y = y0 + r, x = x0c + q;
+    float v = 0.f;
+    if (y >= 0 && y < h && x >= 0 && x < w) {
+      size_t off = ((size_t)y * w + x) * CI + c;
+      v = s_sa[c] * tof(A[off]);
+      if (SKIP) v += s_ss[c] * tof(Sk[off]);
+    }
+    s_x0[p * CIP + c] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < S::R1 * S::C1 * CI; i += blockDim.x) {
+    int c = i % CI, p = i / CI, r = p / S::C1, q = p % S::C1, y = y0 + 1 + r, x = x0c + 1 + q;
+    float v = 0.f;
+    if (y >= 0 && y < h && x >= 0 && x < w) {
+      v = bw.dwb[c];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) v += bw.dw[t * CI + c] * s_x0[((r + t / 3) * S::C0 + q + t % 3) * CIP + c];
+      v = fmaxf(v, 0.f);
+    }
+    s_x1[p * CIP + c] = v;
+  }
+  __syncthreads();
+  constexpr int NPIX = TY * TX, NPH = NPIX / 4, NG = CO / 8;
+  for (int it = threadIdx.x; it < NPIX * NG; it += blockDim.x) {
+    int g = it / NPIX, p = it % NPIX, ph = p / NPH, r = p % NPH;
+    int py = ph >> 1, px = ph & 1;
+    int al = r / (TX / 2), bl = r % (TX / 2);
+    int ty = 2 * al + py, tx = 2 * bl + px;
+    float am[8], ar[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      am[o] = bw.b2[g * 8 + o];
+      ar[o] = bw.rb[g * 8 + o];
+    }
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+      int sy = st >> 1, sx = st & 1, dy = sy - 1 + py, dx = sx - 1 + px;
+      const float* v1 = s_x1 + ((al + 1 + dy) * S::C1 + bl + 1 + dx) * CIP;
+      const float* v0 = s_x0 + ((al + 2 + dy) * S::C0 + bl + 2 + dx) * CIP;
+      size_t wo = ((size_t)(ph * 4 + st) * CI) * CO + g * 8;
+      const float4* wm = reinterpret_cast<const float4*>(bw.w2 + wo);
+      const float4* wr = reinterpret_cast<const float4*>(bw.rw + wo);
+#pragma unroll 4
+      for (int ci = 0; ci < CI; ++ci) {
+        float x1v = v1[ci], x0v = v0[ci];
+        float4 m0 = __ldg(wm + ci * (CO / 4)), m1 = __ldg(wm + ci * (CO / 4) + 1);
+        float4 r0 = __ldg(wr + ci * (CO / 4)), r1 = __ldg(wr + ci * (CO / 4) + 1);
+        am[0] += x1v * m0.x; am[1] += x1v * m0.y; am[2] += x1v * m0.z; am[3] += x1v * m0.w;
+        am[4] += x1v * m1.x; am[5] += x1v * m1.y; am[6] += x1v * m1.z; am[7] += x1v * m1.w;
+        ar[0] += x0v * r0.x; ar[1] += x0v * r0.y; ar[2] += x0v * r0.z; ar[3] += x0v * r0.w;
+        ar[4] += x0v * r1.x; ar[5] += x0v * r1.y; ar[6] += x0v * r1.z; ar[7] += x0v * r1.w;
+      }
+    }
+    int Y = Y0 + ty, X = X0 + tx;
+    bool valid = Y < Ho && X < Wo;
+    T* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO + g * 8;
+    int sp = ty * TX + tx;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      float v = fmaxf(am[o], 0.f) + ar[o];
+      s_o[sp * CO + g * 8 + o] = valid ? v : 0.f;
+      if (valid) dst[o] = fromf<T>(v);
+    }
+  }
+  __syncthreads();
+  int tiles = gridDim.x * gridDim.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
+  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO);
+}
+
+template <typename T>
+struct OutArgs {
+  const T* A;  // D3 pre-ECA output [B][H][W][8]
+  const float* Apart;
+  const float* Ak3;
+  int Atiles;
+  int H, W;
+  NetW w;
+  T* out;  // [B][H][W]
+};
+
+constexpr int kOutTY = 16, kOutTX = 16;
+
+// Output module (reading): ECA weights of D3 applied on load, conv3x3 8 -> 1
+// with bias, sigmoid; one pixel per thread.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_out(OutArgs<T> a) {
+  constexpr int R = kOutTY + 2, C = kOutTX + 2, CP = 9;
+  __shared__ float s_x[R * C * CP];
+  __shared__ float s_g[64], s_s[64];
+  const int b = blockIdx.z, H = a.H, W = a.W;
+  const int Y0 = blockIdx.y * kOutTY, X0 = blockIdx.x * kOutTX;
+  eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_g, s_s);
+  const T* A = a.A + (size_t)b * H * W * 8;
+  for (int i = threadIdx.x; i < R * C * 8; i += blockDim.x) {
+    int c = i & 7, p = i >> 3, r = p / C, q = p % C, y = Y0 - 1 + r, x = X0 - 1 + q;
+    s_x[p * CP + c] = (y >= 0 && y < H && x >= 0 && x < W) ? s_s[c] * tof(A[((size_t)y * W + x) * 8 + c]) : 0.f;
+  }
+  __syncthreads();
+  int ty = threadIdx.x / kOutTX, tx = threadIdx.x % kOutTX;
+  int Y = Y0 + ty, X = X0 + tx;
+  if (Y < H && X < W) {
+    float z = a.w.out_b[0];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) z += a.w.out_w[t * 8 + c] * s_x[((ty + t / 3) * C + tx + t % 3) * CP + c];
+    a.out[((size_t)b * H + Y) * W + X] = fromf<T>(1.f / (1.f + expf(-z)));
+  }
+}
+
+// Tile shapes of the kernels producing each block output.
+constexpr int kTY[6] = {8, 8, 8, 8, 8, 16};
+constexpr int kTX[6] = {16, 16, 8, 16, 16, 16};
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+void block_out_dims(int l, int H, int W, int* ho, int* wo) {
+  static const int div[6] = {2, 4, 8, 4, 2, 1};
+  *ho = H / div[l];
+  *wo = W / div[l];
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t scratch_bytes(int B, int H, int W, size_t elem) {
+  size_t tot = 0;
+  for (int l = 0; l < 6; ++l) {
+    int ho, wo;
+    block_out_dims(l, H, W, &ho, &wo);
+    size_t a = (size_t)B * ho * wo * kBlkCout[l] * elem;
+    size_t p = (size_t)B * cdiv(ho, kTY[l]) * cdiv(wo, kTX[l]) * kBlkCout[l] * sizeof(float);
+    tot += (a + 255) / 256 * 256 + (p + 255) / 256 * 256;
+  }
+  return tot;
+}
+
+void scratch_carve(void* base, int B, int H, int W, size_t elem, FwdScratch* s) {
+  char* p = (char*)base;
+  for (int l = 0; l < 6; ++l) {
+    int ho, wo;
+    block_out_dims(l, H, W, &ho, &wo);
+    s->tiles[l] = cdiv(ho, kTY[l]) * cdiv(wo, kTX[l]);
+    size_t a = (size_t)B * ho * wo * kBlkCout[l] * elem;
+    size_t q = (size_t)B * s->tiles[l] * kBlkCout[l] * sizeof(float);
+    s->act[l] = p;
+    p += (a + 255) / 256 * 256;
+    s->part[l] = (float*)p;
+    p += (q + 255) / 256 * 256;
+  }
+}
+
+template <typename T>
+cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W, const FwdScratch& s,
+                         cudaStream_t st, KernelHook* hook) {
+  cudaError_t e;
+  // E1 = stem + encoder block 1
+  {
+    using Sm = EncSmem<8, 8, 16, true>;
+    auto kern = k_enc<T, 8, 8, 16, true>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    EncArgs<T> a{in, nullptr, nullptr, 0, H, W, w, 0, (T*)s.act[0], s.part[0]};
+    hook->begin(K_ENC1, st);
+    kern<<<dim3(cdiv(W / 2, 16), cdiv(H / 2, 8), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    using Sm = EncSmem<16, 8, 16, false>;
+    auto kern = k_enc<T, 16, 8, 16, false>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    EncArgs<T> a{(const T*)s.act[0], s.part[0], w.blk[0].eca, s.tiles[0], H / 2, W / 2, w, 1, (T*)s.act[1],
+                 s.part[1]};
+    hook->begin(K_ENC2, st);
+    kern<<<dim3(cdiv(W / 4, 16), cdiv(H / 4, 8), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    using Sm = EncSmem<32, 8, 8, false>;
+    auto kern = k_enc<T, 32, 8, 8, false>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    EncArgs<T> a{(const T*)s.act[1], s.part[1], w.blk[1].eca, s.tiles[1], H / 4, W / 4, w, 2, (T*)s.act[2],
+                 s.part[2]};
+    hook->begin(K_ENC3, st);
+    kern<<<dim3(cdiv(W / 8, 8), cdiv(H / 8, 8), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    using Sm = DecSmem<64, 8, 16>;
+    auto kern = k_dec<T, 64, 8, 16, false>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    DecArgs<T> a{(const T*)s.act[2], s.part[2], w.blk[2].eca, s.tiles[2], nullptr, nullptr, nullptr, 0,
+                 H / 8, W / 8, w, 3, (T*)s.act[3], s.part[3]};
+    hook->begin(K_DEC1, st);
+    kern<<<dim3(cdiv(W / 4, 16), cdiv(H / 4, 8), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    using Sm = DecSmem<32, 8, 16>;
+    auto kern = k_dec<T, 32, 8, 16, true>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    DecArgs<T> a{(const T*)s.act[3], s.part[3], w.blk[3].eca, s.tiles[3], (const T*)s.act[1], s.part[1],
+                 w.blk[1].eca, s.tiles[1], H / 4, W / 4, w, 4, (T*)s.act[4], s.part[4]};
+    hook->begin(K_DEC2, st);
+    kern<<<dim3(cdiv(W / 2, 16), cdiv(H / 2, 8), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    using Sm = DecSmem<16, 16, 16>;
+    auto kern = k_dec<T, 16, 16, 16, true>;
+    if ((e = set_smem(kern, Sm::bytes))) return e;
+    DecArgs<T> a{(const T*)s.act[4], s.part[4], w.blk[4].eca, s.tiles[4], (const T*)s.act[0], s.part[0],
+                 w.blk[0].eca, s.tiles[0], H / 2, W / 2, w, 5, (T*)s.act[5], s.part[5]};
+    hook->begin(K_DEC3, st);
+    kern<<<dim3(cdiv(W, 16), cdiv(H, 16), B), kThreads, Sm::bytes, st>>>(a);
+    hook->end(st);
+  }
+  {
+    OutArgs<T> a{(const T*)s.act[5], s.part[5], w.blk[5].eca, s.tiles[5], H, W, w, out};
+    hook->begin(K_OUT, st);
+    k_out<T><<<dim3(cdiv(W, kOutTX), cdiv(H, kOutTY), B), kThreads, 0, st>>>(a);
+    hook->end(st);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t forward_simt<float>(const NetW&, const float*, float*, int, int, int, const FwdScratch&,
+                                         cudaStream_t, KernelHook*);
+template cudaError_t forward_simt<__nv_bfloat16>(const NetW&, const __nv_bfloat16*, __nv_bfloat16*, int, int,
+                                                 int, const FwdScratch&, cudaStream_t, KernelHook*);
+
+}  // namespace stda

@@ -1,0 +1,216 @@
+"""Thin Python binding of libstda (argument marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch
+tensors only carry device memory and streams. Loading fails loudly when
+libstda.so has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstda.so")
+
+OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED, WARMUP = range(9)
+FP32, BF16, FP8_E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8_E4M3}
+MAX_TGT = 16
+
+
+class StdaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"libstda status {status}: {msg}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("max_batch", ctypes.c_int), ("prec", ctypes.c_int),
+                ("weight_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class GenConfig(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("P", ctypes.c_int), ("Q", ctypes.c_int),
+                ("tmin", ctypes.c_int), ("tmax", ctypes.c_int), ("imin", ctypes.c_int), ("imax", ctypes.c_int),
+                ("snr_min", ctypes.c_double), ("snr_max", ctypes.c_double),
+                ("inr_min", ctypes.c_double), ("inr_max", ctypes.c_double),
+                ("kmin", ctypes.c_double), ("kmax", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """The loaded libstda (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libstda.so is missing ({LIB_PATH}); build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        L.stda_status_string.restype = ctypes.c_char_p
+        L.stda_status_string.argtypes = [ctypes.c_int]
+        L.stda_num_params.restype = ctypes.c_size_t
+        L.stda_num_buffers.restype = ctypes.c_size_t
+        L.stda_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_VP)]
+        L.stda_destroy.argtypes = [_VP]
+        for n in ("stda_get_params", "stda_set_params", "stda_get_buffers", "stda_set_buffers"):
+            getattr(L, n).argtypes = [_VP, _VP, ctypes.c_size_t]
+        L.stda_init_params.argtypes = [ctypes.c_uint64, _VP, _VP]
+        L.stda_forward.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
+        L.stda_device_status.argtypes = [_VP]
+        L.stda_last_error.restype = ctypes.c_char_p
+        L.stda_last_error.argtypes = [_VP]
+        L.stda_profile.argtypes = [_VP, ctypes.c_int]
+        L.stda_profile_read.restype = ctypes.c_int
+        L.stda_profile_read.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
+        L.stda_launch_count.restype = ctypes.c_uint64
+        L.stda_launch_count.argtypes = [_VP]
+        L.stda_generate.argtypes = [ctypes.POINTER(GenConfig), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]
+        _lib = L
+    return _lib
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def num_params():
+    return int(lib().stda_num_params())
+
+
+def num_buffers():
+    return int(lib().stda_num_buffers())
+
+
+def init_params(seed=0):
+    """Host-side: the parameters and BN buffers stda_create draws from a seed."""
+    p = np.empty(num_params(), np.float32)
+    b = np.empty(num_buffers(), np.float32)
+    st = lib().stda_init_params(seed, p.ctypes.data, b.ctypes.data)
+    if st != OK:
+        raise StdaError(st)
+    return p, b
+
+
+class Context:
+    """One libstda context: folded weights and activation scratch on the
+    current CUDA device for up to max_batch windows of H x W."""
+
+    def __init__(self, H, W, max_batch, precision="fp32", weight_seed=0, mem_budget_bytes=0):
+        self.precision = precision
+        self.prec = PRECISIONS[precision]
+        self.H, self.W, self.max_batch = H, W, max_batch
+        cfg = Config(H, W, max_batch, self.prec, weight_seed, mem_budget_bytes)
+        h = _VP()
+        st = lib().stda_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise StdaError(st, lib().stda_status_string(st).decode())
+        self.h = h
+
+    @property
+    def io_dtype(self):
+        import torch
+
+        return torch.float32 if self.prec == FP32 else torch.bfloat16
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stda_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise StdaError(st, lib().stda_last_error(self.h).decode())
+
+    def get_params(self):
+        a = np.empty(num_params(), np.float32)
+        self._check(lib().stda_get_params(self.h, a.ctypes.data, a.size))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, np.float32)
+        self._check(lib().stda_set_params(self.h, a.ctypes.data, a.size))
+
+    def get_buffers(self):
+        a = np.empty(num_buffers(), np.float32)
+        self._check(lib().stda_get_buffers(self.h, a.ctypes.data, a.size))
+        return a
+
+    def set_buffers(self, a):
+        a = np.ascontiguousarray(a, np.float32)
+        self._check(lib().stda_set_buffers(self.h, a.ctypes.data, a.size))
+
+    def forward_raw(self, x, out, B, H, W, stream=None):
+        """stda_forward on existing device tensors; returns the status."""
+        return lib().stda_forward(self.h, _ptr(x), _ptr(out), B, H, W, _stream(stream))
+
+    def forward(self, x, out=None, stream=None):
+        """x: CUDA tensor [B][3][H][W] (float32 for fp32, bfloat16 otherwise)."""
+        import torch
+
+        assert x.is_cuda and x.is_contiguous() and x.dtype == self.io_dtype and x.dim() == 4 and x.shape[1] == 3
+        B, _, H, W = x.shape
+        if out is None:
+            out = torch.empty((B, 1, H, W), dtype=x.dtype, device=x.device)
+        self._check(self.forward_raw(x, out, B, H, W, stream))
+        return out
+
+    def profile(self, enable=True):
+        self._check(lib().stda_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last read."""
+        n = 32
+        names = (ctypes.c_char_p * n)()
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        k = lib().stda_profile_read(self.h, names, ms, cnt, n)
+        if k < 0:
+            raise StdaError(ERR_CUDA, "profile_read failed")
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}
+
+    def launch_count(self):
+        return int(lib().stda_launch_count(self.h))
+
+    def device_status(self):
+        return lib().stda_device_status(self.h)
+
+
+def gen_config(g) -> GenConfig:
+    return GenConfig(g.N, g.M, g.P, g.Q, g.tmin, g.tmax, g.imin, g.imax, g.snr_min, g.snr_max, g.inr_min,
+                     g.inr_max, g.kmin, g.kmax)
+
+
+def generate(g, seed, cid, w0, B, dtype=None, with_clean=True, device="cuda", stream=None):
+    """GPU generator: (noisy [B][3][P][Q], clean [B][1][P][Q] | None, bins [B][16][2], ntgt [B])."""
+    import torch
+
+    dtype = dtype or torch.float32
+    noisy = torch.empty((B, 3, g.P, g.Q), dtype=dtype, device=device)
+    clean = torch.empty((B, 1, g.P, g.Q), dtype=dtype, device=device) if with_clean else None
+    bins = torch.empty((B, MAX_TGT, 2), dtype=torch.int32, device=device)
+    ntgt = torch.empty((B,), dtype=torch.int32, device=device)
+    cfg = gen_config(g)
+    st = lib().stda_generate(ctypes.byref(cfg), seed, cid, w0, B, int(dtype == torch.bfloat16), _ptr(noisy),
+                             _ptr(clean), _ptr(bins), _ptr(ntgt), _stream(stream))
+    if st != OK:
+        raise StdaError(st, lib().stda_status_string(st).decode())
+    return noisy, clean, bins, ntgt
