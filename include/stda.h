@@ -110,6 +110,36 @@ stda_status stda_device_status(stda_ctx* ctx);
 const char* stda_last_error(stda_ctx* ctx);
 const char* stda_status_string(stda_status s);
 
+/* ------------------------------------------------------- no-allocation path */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: real-time pipelines that forbid allocation
+ * after start-up (cudaMalloc can synchronise the device and stall for
+ * milliseconds), plug-ins whose host application owns every device buffer,
+ * and code that must stay inside a fixed memory budget.
+ *
+ * The same FP32 forward pass as stda_forward on a context of precision
+ * STDA_FP32, but with no context and no allocation of any kind: the caller
+ * passes the canonical parameters and BN buffers already in device memory
+ *   d_params  [137915] float, d_buffers [1360] float (stda_init_params order)
+ * and the input / output windows (d_in [B][3][H][W], d_out [B][1][H][W],
+ * float). The folded weights and all activation scratch live in one
+ * file-scope device array of 8 MiB that every GPU loading the library holds
+ * until the process exits; it fits up to 65,536 map pixels per call (B*H*W,
+ * e.g. one 256 x 256 window or sixteen 64 x 64 windows). Larger calls return
+ * STDA_ERR_SHAPE without launching anything.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture. Every call on a device shares the one array and overwrites it:
+ * calls whose work overlaps on the GPU (different streams, or different
+ * host threads without ordering) race and corrupt each other's results.
+ * Nothing in the array needs to start at zero: each call writes every value
+ * it later reads. */
+stda_status stda_forward_static(const float* d_params, const float* d_buffers,
+                                const float* d_in, float* d_out, int B, int H,
+                                int W, struct CUstream_st* stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Per-kernel timing: while enabled, every kernel the context launches is

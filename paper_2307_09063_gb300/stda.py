@@ -64,6 +64,7 @@ def lib():
         L.stda_device_status.argtypes = [_VP]
         L.stda_last_error.restype = ctypes.c_char_p
         L.stda_last_error.argtypes = [_VP]
+        L.stda_forward_static.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_profile.argtypes = [_VP, ctypes.c_int]
         L.stda_profile_read.restype = ctypes.c_int
         L.stda_profile_read.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int]
@@ -192,6 +193,21 @@ class Context:
 
     def device_status(self):
         return lib().stda_device_status(self.h)
+
+
+def forward_static(d_params, d_buffers, x, out=None, stream=None):
+    """stda_forward_static: the FP32 forward without a context or any device
+    allocation (for callers that cannot allocate); all tensors on the GPU."""
+    import torch
+
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.dim() == 4
+    B, _, H, W = x.shape
+    if out is None:
+        out = torch.empty((B, 1, H, W), dtype=torch.float32, device=x.device)
+    st = lib().stda_forward_static(_ptr(d_params), _ptr(d_buffers), _ptr(x), _ptr(out), B, H, W, _stream(stream))
+    if st != OK:
+        raise StdaError(st, lib().stda_status_string(st).decode())
+    return out
 
 
 def gen_config(g) -> GenConfig:
