@@ -2,11 +2,13 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "stda_internal.h"
+#include "stda_tc.h"
 
 namespace stda {
 
@@ -326,6 +328,10 @@ struct stda_ctx {
   stda::FoldedOffsets off;
   float* d_folded = nullptr;
   stda::NetW net;
+  unsigned char* d_tc = nullptr;  // packed tensor-core weights and K-step tables
+  stda::TcPackOffsets tc_off;
+  stda::TcWeights tcw;
+  bool force_simt = false;  // STDA_FORCE_SIMT=1: BF16 on the CUDA-core kernels
   void* d_scratch = nullptr;
   size_t scratch_size = 0;
   int* d_status = nullptr;
@@ -354,6 +360,12 @@ stda_status upload_weights(stda_ctx* c) {
   cudaError_t e = cudaMemcpy(c->d_folded, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e) return cuda_fail(c, e, "upload weights");
   c->net = stda::net_from(c->d_folded, c->off);
+  std::vector<unsigned char> blob;
+  stda::pack_tc(host.data(), c->off, &blob, &c->tc_off);
+  if (!c->d_tc && (e = cudaMalloc((void**)&c->d_tc, blob.size()))) return cuda_fail(c, e, "alloc tc weights");
+  if ((e = cudaMemcpy(c->d_tc, blob.data(), blob.size(), cudaMemcpyHostToDevice)))
+    return cuda_fail(c, e, "upload tc weights");
+  c->tcw = stda::tc_weights_from(c->d_tc, c->tc_off);
   return STDA_OK;
 }
 
@@ -390,6 +402,8 @@ stda_status stda_create(const stda_config* cfg, stda_ctx** out) {
   stda_ctx* c = new stda_ctx;
   c->cfg = *cfg;
   cudaGetDevice(&c->device);
+  const char* fs = getenv("STDA_FORCE_SIMT");
+  c->force_simt = fs && fs[0] == '1';
   c->params.resize(stda::kNumParams);
   c->buffers.resize(stda::kNumBuffers);
   stda::init_params(cfg->weight_seed, c->params.data(), c->buffers.data());
@@ -424,6 +438,7 @@ stda_status stda_destroy(stda_ctx* c) {
   if (c->d_folded) cudaFree(c->d_folded);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_tc) cudaFree(c->d_tc);
   delete c;
   return STDA_OK;
 }
@@ -478,8 +493,17 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
       e = stda::forward_simt<float>(c->net, (const float*)d_in, (float*)d_out, B, H, W, s, st, &c->prof);
       break;
     case STDA_BF16:
-      e = stda::forward_simt<__nv_bfloat16>(c->net, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W,
-                                            s, st, &c->prof);
+      if (c->force_simt) {
+        e = stda::forward_simt<__nv_bfloat16>(c->net, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H,
+                                              W, s, st, &c->prof);
+      } else {
+        int tiles[6];
+        e = stda::forward_tc(c->net, c->tcw, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W, s,
+                             c->d_status, st, &c->prof, tiles);
+        if (!e)
+          e = stda::launch_out_bf16(c->net, (const __nv_bfloat16*)s.act[5], s.part[5], tiles[5],
+                                    (__nv_bfloat16*)d_out, B, H, W, st, &c->prof);
+      }
       break;
     default:
       return fail(c, STDA_ERR_UNSUPPORTED, "forward: precision not built yet");

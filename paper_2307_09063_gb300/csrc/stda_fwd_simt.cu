@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 
 #include "stda_internal.h"
+#include "stda_tc.h"
 
 namespace stda {
 namespace {
@@ -384,6 +385,13 @@ void block_out_dims(int l, int H, int W, int* ho, int* wo) {
   *wo = W / div[l];
 }
 
+// Partial-sum slots per window: the CUDA-core kernels' 2-D tiles, or the
+// tensor-core kernels' row bands (at most one per output row).
+int part_tiles(int l, int ho, int wo) {
+  int t = cdiv(ho, kTY[l]) * cdiv(wo, kTX[l]);
+  return t > ho ? t : ho;
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -397,7 +405,7 @@ size_t scratch_bytes(int B, int H, int W, size_t elem) {
     int ho, wo;
     block_out_dims(l, H, W, &ho, &wo);
     size_t a = (size_t)B * ho * wo * kBlkCout[l] * elem;
-    size_t p = (size_t)B * cdiv(ho, kTY[l]) * cdiv(wo, kTX[l]) * kBlkCout[l] * sizeof(float);
+    size_t p = (size_t)B * part_tiles(l, ho, wo) * kBlkCout[l] * sizeof(float);
     tot += (a + 255) / 256 * 256 + (p + 255) / 256 * 256;
   }
   return tot;
@@ -410,7 +418,7 @@ void scratch_carve(void* base, int B, int H, int W, size_t elem, FwdScratch* s) 
     block_out_dims(l, H, W, &ho, &wo);
     s->tiles[l] = cdiv(ho, kTY[l]) * cdiv(wo, kTX[l]);
     size_t a = (size_t)B * ho * wo * kBlkCout[l] * elem;
-    size_t q = (size_t)B * s->tiles[l] * kBlkCout[l] * sizeof(float);
+    size_t q = (size_t)B * part_tiles(l, ho, wo) * kBlkCout[l] * sizeof(float);
     s->act[l] = p;
     p += (a + 255) / 256 * 256;
     s->part[l] = (float*)p;
@@ -488,6 +496,15 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
     k_out<T><<<dim3(cdiv(W, kOutTX), cdiv(H, kOutTY), B), kThreads, 0, st>>>(a);
     hook->end(st);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
+                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook) {
+  OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
+  hook->begin(K_OUT, st);
+  k_out<__nv_bfloat16><<<dim3(cdiv(W, kOutTX), cdiv(H, kOutTY), B), kThreads, 0, st>>>(a);
+  hook->end(st);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,76 @@
+// Tensor-core forward path: shared declarations (host and device).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "stda_internal.h"
+
+namespace stda {
+
+// One K-step (K = 16 bf16) of an implicit-GEMM accumulator: the two 8-wide
+// K halves read plane pl0 / pl1 of the staged activations at pixel offset
+// (dr, dc) from the GEMM row's own pixel.
+struct KStep {
+  int8_t pl0, dr0, dc0, pl1, dr1, dc1, pad0, pad1;
+};
+
+// Packed stage-2 weights of one block in the MMA's K-major core-matrix
+// order, [accumulator phase][K-step][K half][N padded][8] bf16, and the
+// K-step table ([phase][K-step]).
+struct TcLayer {
+  const __nv_bfloat16* wm;
+  const __nv_bfloat16* wr;
+  const KStep* ks;
+};
+struct TcWeights {
+  TcLayer layer[6];
+};
+
+constexpr int kTcMiscBytes = 7424;
+constexpr int kTcMaxSmem = 227 * 1024;
+
+struct TcArgs {
+  const __nv_bfloat16* in;  // block 1: raw frames [B][3][H][W]; else previous block [B][h][w][CI]
+  const float* ppart;
+  const float* pk3;
+  int ptiles;
+  const __nv_bfloat16* skip;  // decoder skip operand [B][h][w][CI] (pre-ECA) or null
+  const float* spart;
+  const float* sk3;
+  int stiles;
+  int h, w;       // input map of this block
+  int band;       // encoder: output rows per CTA; decoder: input rows per CTA
+  int ntile;      // 128-row GEMM tiles per CTA
+  int WP, PIXA;   // plane pitch and pixels per plane
+  int tiles_per_window;
+  uint32_t tmem_cols;
+  const float *stem_w, *stem_b, *dw, *dwb, *b2, *rb;
+  TcLayer L;
+  __nv_bfloat16* out;
+  float* part;
+  int* status;
+};
+
+// Host: packs the folded FP32 weights of every block for the tensor cores.
+// Returns byte offsets (into one device buffer) of each block's tensors.
+struct TcPackOffsets {
+  size_t wm[6], wr[6], ks[6];
+  size_t total;
+};
+void pack_tc(const float* folded, const FoldedOffsets& off, std::vector<unsigned char>* blob,
+             TcPackOffsets* po);
+TcWeights tc_weights_from(const unsigned char* dev_base, const TcPackOffsets& po);
+
+// Forward of the six blocks on the tensor cores (output conv excluded);
+// tiles_out receives the ECA partial-sum tiles per window of each block.
+cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* in, __nv_bfloat16* out, int B,
+                       int H, int W, const FwdScratch& s, int* status, cudaStream_t st, KernelHook* hook,
+                       int* tiles_out);
+
+// Output conv (CUDA cores) over the decoder-3 map, bf16 I/O.
+cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
+                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook);
+
+}  // namespace stda

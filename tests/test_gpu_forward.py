@@ -105,6 +105,32 @@ def test_bf16_forward_full_batch_256x128(stda, weights):
         assert abs(_sinr(got, obins) - _sinr(z32, obins)) <= SINR_DB_TOL
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 24, 40), (1, 8, 8), (2, 72, 136), (1, 64, 64), (1, 128, 64), (1, 512, 256)])
+def test_bf16_tensor_core_forward_shapes(stda, weights, B, H, W):
+    """Tensor-core BF16 path against the oracle on shapes with ragged bands
+    and GEMM tiles at every level (8 x 8 minimum up to the 512 x 256 map)."""
+    rng = np.random.default_rng(H * 7 + W)
+    x = bf16_round(rng.uniform(0, 1, (B, 3, H, W)))
+    ref = O.forward_batch(*weights, x)
+    ctx = stda.Context(H, W, B, "bf16", 0)
+    got = ctx.forward(torch.from_numpy(x).cuda().to(torch.bfloat16))[:, 0].float().cpu().numpy()
+    assert ctx.device_status() == stda.OK
+    assert np.max(np.abs(got - ref)) <= BF16_ATOL
+
+
+def test_bf16_tensor_core_matches_cuda_core_path(stda, monkeypatch):
+    """The tcgen05 path and the CUDA-core path of the same BF16 context agree
+    within the BF16 tolerance. They are not closer than that: the tensor-core
+    path rounds the stem and stage-1 outputs to bf16 (they are MMA operands),
+    the CUDA-core path keeps them in FP32 shared memory."""
+    rng = np.random.default_rng(17)
+    x = torch.from_numpy(rng.uniform(0, 1, (4, 3, 64, 96)).astype(np.float32)).cuda().to(torch.bfloat16)
+    tc = stda.Context(64, 96, 4, "bf16", 0).forward(x).float()
+    monkeypatch.setenv("STDA_FORCE_SIMT", "1")
+    simt = stda.Context(64, 96, 4, "bf16", 0).forward(x).float()
+    assert (tc - simt).abs().max().item() <= BF16_ATOL
+
+
 def test_invalid_calls_return_status(stda):
     ctx = stda.Context(32, 32, 2, "fp32", 0)
     x = torch.zeros((2, 3, 32, 32), device="cuda")
