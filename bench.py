@@ -38,8 +38,14 @@ UNIT = "frames/s"
 KERNEL_MACS_PER_PX = {"enc1_stem": 864, "enc2": 612, "enc3": 594, "dec1": 1033, "dec2": 1042,
                       "dec3": 1060, "out": 72}
 MACS_PER_PX = sum(KERNEL_MACS_PER_PX.values())  # 5277
+# Of those, the dense stage-2 convolutions run on the tensor cores in the
+# bf16 / fp8 paths; the stem, the depthwise stage 1 and the output conv stay
+# on the FP32 FMA pipe.
+KERNEL_TC_MACS_PER_PX = {"enc1_stem": 576, "enc2": 576, "enc3": 576, "dec1": 1024, "dec2": 1024, "dec3": 1024,
+                         "out": 0}
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.070
 FFMA_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ / 1e3  # 80.5
+FP8_OVER_BF16 = 4.5 / 2.25  # nominal dense ratio
 
 
 def load_peaks():
@@ -179,7 +185,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bf16_b256_3x256x128")
+    ap.add_argument("--workload", default="bf16_b256_3x256x128",
+                    help="bf16_b256_3x256x128 | fp8_b1024_3x512x256 | fp32_b1_3x64x64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -276,20 +283,33 @@ def main():
     hbm_gbs, bf16_tf, bf16_tf_sus, peak_src = load_peaks()
     bytes_per_step = B * 4 * H * W * esz  # 3 input maps + 1 output map per window
     hbm_achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
-    # dominant kernel by measured time share
+    # dominant kernel by measured time share; its FMA-pipe and tensor-pipe
+    # fractions, the larger one naming the bound
     name = max(kt, key=lambda k: kt[k][0])
     k_ms, k_n = kt[name]
     k_avg_s = k_ms / max(k_n, 1) / 1e3
-    flops = 2.0 * KERNEL_MACS_PER_PX[name] * B * H * W
-    achieved_tf = flops / k_avg_s / 1e12
+    px = B * H * W
+    tc_macs = KERNEL_TC_MACS_PER_PX[name] if w.precision != "fp32" else 0
+    fma_macs = KERNEL_MACS_PER_PX[name] - tc_macs
+    alu_tf = 2.0 * fma_macs * px / k_avg_s / 1e12
+    tc_tf = 2.0 * tc_macs * px / k_avg_s / 1e12
+    tc_peak = bf16_tf * (FP8_OVER_BF16 if w.precision.startswith("fp8") else 1.0)
+    fr_alu, fr_tc = alu_tf / FFMA_PEAK_TFLOPS, tc_tf / tc_peak
     shares = {k: round(v[0] / max(sum(u[0] for u in kt.values()), 1e-12), 4) for k, v in kt.items()}
-    roofline = {"kernel": name, "bound": "alu", "achieved": achieved_tf, "peak": FFMA_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tf / FFMA_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz",
-                "flops_per_launch": flops, "avg_launch_ms": k_avg_s * 1e3, "time_shares": shares}
+    if fr_tc > fr_alu:
+        bound, ach, peak, psrc = "tensor", tc_tf, tc_peak, (
+            f"{peak_src} bf16 burst {bf16_tf} TFLOP/s" + (" x 2 (fp8/bf16 nominal)" if tc_peak != bf16_tf else ""))
+    else:
+        bound, ach, peak, psrc = "alu", alu_tf, FFMA_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
+    roofline = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": psrc,
+                "alu": {"achieved": alu_tf, "peak": FFMA_PEAK_TFLOPS, "frac": fr_alu,
+                        "flops_per_launch": 2.0 * fma_macs * px},
+                "tensor": {"achieved": tc_tf, "peak": tc_peak, "frac": fr_tc, "flops_per_launch": 2.0 * tc_macs * px},
+                "avg_launch_ms": k_avg_s * 1e3, "time_shares": shares}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if w.precision != "fp32" else "f32",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3x2"}.get(w.precision, w.precision),
             "data": "synthetic (seeded FMCW targets, interferers, noise; GPU generator)",
             "config": {"workload": w.name, "batch": B, "H": H, "W": W, "precision": w.precision,
                        "accumulate": "fp32", "l2": "flushed (256 MB write) between timed steps",

@@ -21,7 +21,7 @@
  *  - A context is not thread-safe: calls on one context must not overlap in
  *    host threads.
  *  - Map layout: a window is [3][H][W] float (STDA_FP32) or bfloat16
- *    (STDA_BF16, STDA_FP8_E4M3), frames ordered t, t-1, t-2 (channel order
+ *    (the other precisions), frames ordered t, t-1, t-2 (channel order
  *    of Eq. "concat_operation"); H = range bins, W = Doppler bins, both
  *    positive multiples of 8 (the three stride-2 stages halve the map three
  *    times). A batch is [B][3][H][W], the output [B][1][H][W] in the same
@@ -55,7 +55,25 @@ typedef enum {
   STDA_WARMUP = 8           /* serving: fewer than three frames buffered  */
 } stda_status;
 
-typedef enum { STDA_FP32 = 0, STDA_BF16 = 1, STDA_FP8_E4M3 = 2 } stda_precision;
+/* Arithmetic of the forward pass (accumulation is FP32 in every case):
+ *  STDA_FP32          FP32 FMA on the CUDA cores, float I/O.
+ *  STDA_BF16          bf16 tensor-core operands (tcgen05 kind::f16), bf16 I/O.
+ *  STDA_FP8_E4M3      E4M3 tensor-core operands (kind::f8f6f4) for the dense
+ *                     convolutions of blocks 2-6, weights with per-output-
+ *                     channel scales; every operand is a two-term E4M3 sum
+ *                     (high part + E4M3 of its rounding remainder) and each
+ *                     tap issues three MMAs (hi*hi, lo*hi, hi*lo), which keeps
+ *                     the error at the bf16 level. Block 1 (8 input channels)
+ *                     runs in bf16. bf16 I/O.
+ *  STDA_FP8_E4M3_FAST as STDA_FP8_E4M3 with one E4M3 term per operand (one
+ *                     MMA per tap); about 16x the bf16 error (3-bit mantissa),
+ *                     outside the bf16 tolerance. */
+typedef enum {
+  STDA_FP32 = 0,
+  STDA_BF16 = 1,
+  STDA_FP8_E4M3 = 2,
+  STDA_FP8_E4M3_FAST = 3
+} stda_precision;
 
 typedef struct {
   int H, W;          /* largest map size the context serves (multiples of 8) */

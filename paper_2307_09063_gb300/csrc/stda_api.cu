@@ -329,6 +329,7 @@ struct stda_ctx {
   float* d_folded = nullptr;
   stda::NetW net;
   unsigned char* d_tc = nullptr;  // packed tensor-core weights and K-step tables
+  size_t d_tc_bytes = 0;
   stda::TcPackOffsets tc_off;
   stda::TcWeights tcw;
   bool force_simt = false;  // STDA_FORCE_SIMT=1: BF16 on the CUDA-core kernels
@@ -361,8 +362,19 @@ stda_status upload_weights(stda_ctx* c) {
   if (e) return cuda_fail(c, e, "upload weights");
   c->net = stda::net_from(c->d_folded, c->off);
   std::vector<unsigned char> blob;
-  stda::pack_tc(host.data(), c->off, &blob, &c->tc_off);
-  if (!c->d_tc && (e = cudaMalloc((void**)&c->d_tc, blob.size()))) return cuda_fail(c, e, "alloc tc weights");
+  // FP8: E4M3 stage-2 operands in every block but the first (8 input channels)
+  bool f8[6];
+  const bool fp8 = c->cfg.prec == STDA_FP8_E4M3 || c->cfg.prec == STDA_FP8_E4M3_FAST;
+  for (int b = 0; b < 6; ++b) f8[b] = fp8 && b > 0;
+  stda::pack_tc(host.data(), c->off, f8, c->cfg.prec == STDA_FP8_E4M3_FAST ? 1 : 2, &blob, &c->tc_off);
+  if (c->d_tc && blob.size() > c->d_tc_bytes) {
+    cudaFree(c->d_tc);
+    c->d_tc = nullptr;
+  }
+  if (!c->d_tc) {
+    if ((e = cudaMalloc((void**)&c->d_tc, blob.size()))) return cuda_fail(c, e, "alloc tc weights");
+    c->d_tc_bytes = blob.size();
+  }
   if ((e = cudaMemcpy(c->d_tc, blob.data(), blob.size(), cudaMemcpyHostToDevice)))
     return cuda_fail(c, e, "upload tc weights");
   c->tcw = stda::tc_weights_from(c->d_tc, c->tc_off);
@@ -397,7 +409,8 @@ stda_status stda_create(const stda_config* cfg, stda_ctx** out) {
   if (!cfg || !out) return STDA_ERR_INVALID_ARG;
   *out = nullptr;
   if (!shape_ok(cfg->H, cfg->W) || cfg->max_batch < 1) return STDA_ERR_SHAPE;
-  if (cfg->prec != STDA_FP32 && cfg->prec != STDA_BF16 && cfg->prec != STDA_FP8_E4M3)
+  if (cfg->prec != STDA_FP32 && cfg->prec != STDA_BF16 && cfg->prec != STDA_FP8_E4M3 &&
+      cfg->prec != STDA_FP8_E4M3_FAST)
     return STDA_ERR_INVALID_ARG;
   stda_ctx* c = new stda_ctx;
   c->cfg = *cfg;
@@ -493,7 +506,9 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
       e = stda::forward_simt<float>(c->net, (const float*)d_in, (float*)d_out, B, H, W, s, st, &c->prof);
       break;
     case STDA_BF16:
-      if (c->force_simt) {
+    case STDA_FP8_E4M3:
+    case STDA_FP8_E4M3_FAST:
+      if (c->force_simt || c->cfg.prec == STDA_FP32) {
         e = stda::forward_simt<__nv_bfloat16>(c->net, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H,
                                               W, s, st, &c->prof);
       } else {
@@ -506,7 +521,7 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
       }
       break;
     default:
-      return fail(c, STDA_ERR_UNSUPPORTED, "forward: precision not built yet");
+      return fail(c, STDA_ERR_UNSUPPORTED, "forward: unknown precision");
   }
   if (e) return cuda_fail(c, e, "forward");
   return STDA_OK;

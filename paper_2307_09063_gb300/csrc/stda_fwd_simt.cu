@@ -32,21 +32,29 @@ constexpr int kThreads = 256;
 
 // ECA weights of one window from the per-tile channel sums of the block that
 // produced the map: g = GAP (mean), z = 1-D conv (k = 3, zero padding),
-// s = sigmoid(z).
+// s = sigmoid(z). The tile sums are split over blockDim / C threads per
+// channel and combined in a fixed order; s_tmp holds blockDim floats.
 __device__ void eca_scales(const float* __restrict__ part, int ntiles, int C,
                            float inv_n, const float* __restrict__ k3,
-                           float* s_g, float* s_s) {
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+                           float* s_tmp, float* s_g, float* s_s) {
+  const int P = blockDim.x / C, c = threadIdx.x % C, q = threadIdx.x / C;
+  if (q < P) {
     float a = 0.f;
-    for (int t = 0; t < ntiles; ++t) a += part[t * C + c];
-    s_g[c] = a * inv_n;
+    for (int t = q; t < ntiles; t += P) a += part[t * C + c];
+    s_tmp[q * C + c] = a;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    float z = k3[1] * s_g[c];
-    if (c > 0) z += k3[0] * s_g[c - 1];
-    if (c + 1 < C) z += k3[2] * s_g[c + 1];
-    s_s[c] = 1.f / (1.f + expf(-z));
+  if (threadIdx.x < C) {
+    float a = 0.f;
+    for (int k = 0; k < P; ++k) a += s_tmp[k * C + threadIdx.x];
+    s_g[threadIdx.x] = a * inv_n;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < C; i += blockDim.x) {
+    float z = k3[1] * s_g[i];
+    if (i > 0) z += k3[0] * s_g[i - 1];
+    if (i + 1 < C) z += k3[2] * s_g[i + 1];
+    s_s[i] = 1.f / (1.f + expf(-z));
   }
   __syncthreads();
 }
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
       for (int o = 0; o < 8; ++o) s_x0[i * CIP + o] = inside ? fmaxf(acc[o], 0.f) : 0.f;
     }
   } else {
-    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(H * W), a.pk3, s_g, s_s);
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(H * W), a.pk3, s_o, s_g, s_s);
     const T* in = a.in + (size_t)b * H * W * CI;
     for (int i = threadIdx.x; i < S::R0 * S::C0 * CI; i += blockDim.x) {
       int c = i % CI, p = i / CI, r = p / S::C0, q = p % S::C0, y = y0 + r, x = x0c + q;
@@ -258,8 +266,8 @@ __global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
   const int y0 = Y0 / 2 - 2, x0c = X0 / 2 - 2;
   const BlockW bw = a.wt.blk[a.blk];
   const float inv_n = 1.f / (float)(h * w);
-  eca_scales(a.Apart + (size_t)b * a.Atiles * CI, a.Atiles, CI, inv_n, a.Ak3, s_g, s_sa);
-  if (SKIP) eca_scales(a.Spart + (size_t)b * a.Stiles * CI, a.Stiles, CI, inv_n, a.Sk3, s_g, s_ss);
+  eca_scales(a.Apart + (size_t)b * a.Atiles * CI, a.Atiles, CI, inv_n, a.Ak3, s_o, s_g, s_sa);
+  if (SKIP) eca_scales(a.Spart + (size_t)b * a.Stiles * CI, a.Stiles, CI, inv_n, a.Sk3, s_o, s_g, s_ss);
   const T* A = a.A + (size_t)b * h * w * CI;
   const T* Sk = SKIP ? a.S + (size_t)b * h * w * CI : nullptr;
   for (int i = threadIdx.x; i < S::R0 * S::C0 * CI; i += blockDim.x) {
@@ -351,14 +359,42 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_out(OutArgs<T> a) {
   constexpr int R = kOutTY + 2, C = kOutTX + 2, CP = 9;
   __shared__ float s_x[R * C * CP];
-  __shared__ float s_g[64], s_s[64];
+  __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
+  __shared__ __align__(16) float s_w[72];
+  for (int i = threadIdx.x; i < 72; i += blockDim.x) s_w[i] = a.w.out_w[i];
   const int b = blockIdx.z, H = a.H, W = a.W;
   const int Y0 = blockIdx.y * kOutTY, X0 = blockIdx.x * kOutTX;
-  eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_g, s_s);
+  eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_tmp, s_g, s_s);
   const T* A = a.A + (size_t)b * H * W * 8;
-  for (int i = threadIdx.x; i < R * C * 8; i += blockDim.x) {
-    int c = i & 7, p = i >> 3, r = p / C, q = p % C, y = Y0 - 1 + r, x = X0 - 1 + q;
-    s_x[p * CP + c] = (y >= 0 && y < H && x >= 0 && x < W) ? s_s[c] * tof(A[((size_t)y * W + x) * 8 + c]) : 0.f;
+  if (sizeof(T) == 2) {
+    // one 16-byte load per pixel (8 bf16 channels), two pixels in flight per thread
+    for (int p0 = threadIdx.x; p0 < R * C; p0 += 2 * blockDim.x) {
+      uint4 v[2];
+      bool in[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        int p = p0 + u * blockDim.x, y = Y0 - 1 + p / C, x = X0 - 1 + p % C;
+        in[u] = p < R * C && y >= 0 && y < H && x >= 0 && x < W;
+        v[u] = in[u] ? *(const uint4*)(A + ((size_t)y * W + x) * 8) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        int p = p0 + u * blockDim.x;
+        if (p >= R * C) continue;
+        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float2 f = __bfloat1622float2(hv[k]);
+          s_x[p * CP + 2 * k] = s_s[2 * k] * f.x;
+          s_x[p * CP + 2 * k + 1] = s_s[2 * k + 1] * f.y;
+        }
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < R * C * 8; i += blockDim.x) {
+      int c = i & 7, p = i >> 3, r = p / C, q = p % C, y = Y0 - 1 + r, x = X0 - 1 + q;
+      s_x[p * CP + c] = (y >= 0 && y < H && x >= 0 && x < W) ? s_s[c] * tof(A[((size_t)y * W + x) * 8 + c]) : 0.f;
+    }
   }
   __syncthreads();
   int ty = threadIdx.x / kOutTX, tx = threadIdx.x % kOutTX;
@@ -366,9 +402,12 @@ __global__ void __launch_bounds__(kThreads) k_out(OutArgs<T> a) {
   if (Y < H && X < W) {
     float z = a.w.out_b[0];
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-      for (int c = 0; c < 8; ++c) z += a.w.out_w[t * 8 + c] * s_x[((ty + t / 3) * C + tx + t % 3) * CP + c];
+    for (int t = 0; t < 9; ++t) {
+      const float* xv = &s_x[((ty + t / 3) * C + tx + t % 3) * CP];
+      const float4 wa = *(const float4*)&s_w[t * 8], wb = *(const float4*)&s_w[t * 8 + 4];
+      z += wa.x * xv[0] + wa.y * xv[1] + wa.z * xv[2] + wa.w * xv[3] + wb.x * xv[4] + wb.y * xv[5] +
+           wb.z * xv[6] + wb.w * xv[7];
+    }
     a.out[((size_t)b * H + Y) * W + X] = fromf<T>(1.f / (1.f + expf(-z)));
   }
 }

@@ -1,5 +1,6 @@
 // Radar-STDA forward pass with the dense convolutions on the tcgen05 tensor
-// cores (BF16 operands, FP32 accumulation in tensor memory).
+// cores: BF16 operands (kind::f16) or E4M3 operands with per-output-channel
+// weight scales (kind::f8f6f4), FP32 accumulation in tensor memory.
 //
 // One kernel per network level; one CTA per band of rows of one window,
 // always spanning the full map width. Per CTA:
@@ -21,6 +22,7 @@
 //  4. Epilogue: TMEM -> registers, ReLU(main + BN shift) + residual + bias,
 //     bf16 NHWC store, per-band channel sums for the next ECA.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstring>
@@ -34,7 +36,7 @@ namespace stda {
 namespace {
 
 using namespace umma;
-constexpr int kThreads = 256;
+constexpr int kMaxThreads = 512;
 
 __device__ __forceinline__ void bf16x8_to_f32(uint4 u, float* f) {
   const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
@@ -53,22 +55,108 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
   return u;
 }
 
-// ECA weights of one window (same arithmetic as the CUDA-core path).
+// A 16-byte pixel of a staged plane: 8 bf16 channels, or 16 E4M3 channels.
+template <bool F8>
+struct Op;
+template <>
+struct Op<false> {
+  static constexpr int CG = 8;
+  __device__ static void to_f32(uint4 u, float* f) { bf16x8_to_f32(u, f); }
+  __device__ static uint4 from_f32(const float* f) { return f32_to_bf16x8(f); }
+};
+template <>
+struct Op<true> {
+  static constexpr int CG = 16;
+  __device__ static void to_f32(uint4 u, float* f) {
+    const __nv_fp8x2_storage_t* q = reinterpret_cast<const __nv_fp8x2_storage_t*>(&u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float2 t = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q[i], __NV_E4M3)));
+      f[2 * i] = t.x;
+      f[2 * i + 1] = t.y;
+    }
+  }
+  __device__ static uint4 from_f32(const float* f) {
+    uint4 u;
+    __nv_fp8x2_storage_t* q = reinterpret_cast<__nv_fp8x2_storage_t*>(&u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) q[i] = __nv_cvt_float2_to_fp8x2(make_float2(f[2 * i], f[2 * i + 1]), __NV_SATFINITE, __NV_E4M3);
+    return u;
+  }
+};
+
+// Stores f into a 16-byte pixel (and, for two-term E4M3, its remainder into
+// the matching pixel of the low-term planes `lo_off` bytes further on).
+template <bool F8>
+__device__ __forceinline__ void store_px(uint4* dst, const float* f, int terms, size_t lo_off) {
+  uint4 hi = Op<F8>::from_f32(f);
+  *dst = hi;
+  if (F8 && terms == 2) {
+    constexpr int CG = Op<F8>::CG;
+    float r[CG];
+    Op<F8>::to_f32(hi, r);
+#pragma unroll
+    for (int k = 0; k < CG; ++k) r[k] = f[k] - r[k];
+    *(uint4*)((unsigned char*)dst + lo_off) = Op<F8>::from_f32(r);
+  }
+}
+template <bool F8>
+__device__ __forceinline__ void load_px(const uint4* src, float* f, int terms, size_t lo_off) {
+  Op<F8>::to_f32(*src, f);
+  if (F8 && terms == 2) {
+    constexpr int CG = Op<F8>::CG;
+    float r[CG];
+    Op<F8>::to_f32(*(const uint4*)((const unsigned char*)src + lo_off), r);
+#pragma unroll
+    for (int k = 0; k < CG; ++k) f[k] += r[k];
+  }
+}
+
+// ECA weights of one window: g = GAP from the per-band channel sums, then
+// the 1-D conv (k = 3, zero padding) and the sigmoid. The band sums are
+// split over P = blockDim / C threads per channel and combined in a fixed
+// order (deterministic). s_tmp needs blockDim floats.
 __device__ void eca_scales(const float* __restrict__ part, int ntiles, int C, float inv_n,
-                           const float* __restrict__ k3, float* s_g, float* s_s) {
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+                           const float* __restrict__ k3, float* s_tmp, float* s_g, float* s_s) {
+  const int P = blockDim.x / C, c = threadIdx.x % C, q = threadIdx.x / C;
+  if (q < P) {
     float a = 0.f;
-    for (int t = 0; t < ntiles; ++t) a += part[t * C + c];
-    s_g[c] = a * inv_n;
+    for (int t = q; t < ntiles; t += P) a += part[t * C + c];
+    s_tmp[q * C + c] = a;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    float z = k3[1] * s_g[c];
-    if (c > 0) z += k3[0] * s_g[c - 1];
-    if (c + 1 < C) z += k3[2] * s_g[c + 1];
-    s_s[c] = 1.f / (1.f + expf(-z));
+  if (threadIdx.x < C) {
+    float a = 0.f;
+    for (int k = 0; k < P; ++k) a += s_tmp[k * C + threadIdx.x];
+    s_g[threadIdx.x] = a * inv_n;
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < C; i += blockDim.x) {
+    float z = k3[1] * s_g[i];
+    if (i > 0) z += k3[0] * s_g[i - 1];
+    if (i + 1 < C) z += k3[2] * s_g[i + 1];
+    s_s[i] = 1.f / (1.f + expf(-z));
+  }
+  __syncthreads();
+}
+
+// Runs load(i) for U indices per thread back to back (independent loads in
+// flight together), then use(i, value) for each.
+template <int U, typename L, typename F>
+__device__ __forceinline__ void batched(int n, L load, F use) {
+  for (int base = threadIdx.x; base < n; base += U * blockDim.x) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int i = base + u * blockDim.x;
+      if (i < n) v[u] = load(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int i = base + u * blockDim.x;
+      if (i < n) use(i, v[u]);
+    }
+  }
 }
 
 __device__ __forceinline__ void warp_sum_to(float v, float* dst) {
@@ -81,10 +169,11 @@ __device__ __forceinline__ void warp_sum_to(float v, float* dst) {
 // at TMEM column (i * nacc + a) * NP; K-steps of accumulator a are
 // ks[(a % nph) * nsteps ...] for the main branch (a < nph) and the same
 // table for the residual branch (a >= nph).
+template <bool F8>
 __device__ void issue_mmas(uint32_t tmem, const KStep* ks, int nsteps, int nph, int NP, int ntile, int m_lo,
-                           int WP, int PIXA, uint32_t x1_base, uint32_t x0_base, uint32_t wm_base,
-                           uint32_t wr_base) {
-  const uint32_t idesc = idesc_bf16(128, NP);
+                           int WP, int PIXA, int terms, uint32_t a_lo_off, uint32_t b_lo_off, uint32_t x1_base,
+                           uint32_t x0_base, uint32_t wm_base, uint32_t wr_base) {
+  const uint32_t idesc = F8 ? idesc_e4m3(128, NP) : idesc_bf16(128, NP);
   const uint32_t wstep = 2u * NP * 16u;  // bytes per packed K-step
   for (int i = 0; i < ntile; ++i) {
     int m0 = m_lo + 128 * i;
@@ -97,9 +186,18 @@ __device__ void issue_mmas(uint32_t tmem, const KStep* ks, int nsteps, int nph, 
         KStep k = ks[ph * nsteps + j];
         int p0 = k.pl0 * PIXA + m0 + k.dr0 * WP + k.dc0;
         int p1 = k.pl1 * PIXA + m0 + k.dr1 * WP + k.dc1;
-        uint64_t ad = desc(xb + (uint32_t)p0 * 16u, (uint32_t)(p1 - p0) * 16u, 128);
-        uint64_t bd = desc(wb + (uint32_t)(ph * nsteps + j) * wstep, (uint32_t)NP * 16u, 128);
-        mma_bf16(d, ad, bd, idesc, j > 0);
+        uint32_t aa = xb + (uint32_t)p0 * 16u, lbo = (uint32_t)(p1 - p0) * 16u;
+        uint32_t bb = wb + (uint32_t)(ph * nsteps + j) * wstep;
+        if (F8) {
+          // two-term operands: hi*hi + lo*hi + hi*lo
+          mma_f8(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+          if (terms == 2) {
+            mma_f8(d, desc(aa + a_lo_off, lbo, 128), desc(bb, NP * 16u, 128), idesc, 1);
+            mma_f8(d, desc(aa, lbo, 128), desc(bb + b_lo_off, NP * 16u, 128), idesc, 1);
+          }
+        } else {
+          mma_bf16(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+        }
       }
     }
   }
@@ -110,10 +208,11 @@ struct Smem {
   int wbytes, planes_bytes, in_bytes;
   int off_wm, off_wr, off_x0, off_x1, off_in, off_misc, total;
 };
-__host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplanes, int PIXA, int in_bytes) {
+__host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplanes, int PIXA, int in_bytes,
+                                            int terms = 1) {
   Smem s;
-  s.wbytes = nsteps_total * 2 * NP * 16;
-  s.planes_bytes = nplanes * PIXA * 16;
+  s.wbytes = terms * nsteps_total * 2 * NP * 16;
+  s.planes_bytes = terms * nplanes * PIXA * 16;
   s.in_bytes = (in_bytes + 127) / 128 * 128;
   s.off_wm = 0;
   s.off_wr = s.wbytes;
@@ -127,8 +226,8 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
 
 // Misc area: [0, 512) K-step table, [512, 1024) ECA g / s (input),
 // [1024, 1536) ECA s (skip), [1536, 4096) stage-1 weights + bias,
-// [4096, 5120) stem weights + bias, [5120, 7168) per-warp channel sums,
-// [7168] mbarrier, [7176] TMEM slot.
+// [4096, 5120) stem weights + bias, [5120, 9216) per-warp channel sums
+// (up to 16 warps), [9216] mbarrier, [9224] TMEM slot.
 struct Misc {
   KStep* ks;
   float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red;
@@ -144,15 +243,15 @@ struct Misc {
     stw = (float*)(p + 4096);
     stb = stw + 216;
     red = (float*)(p + 5120);
-    bar = (uint64_t*)(p + 7168);
-    tslot = (uint32_t*)(p + 7176);
+    bar = (uint64_t*)(p + 9216);
+    tslot = (uint32_t*)(p + 9224);
   }
 };
 
 __device__ void copy_to_smem(void* dst, const void* src, int bytes) {
   const uint4* s = (const uint4*)src;
   uint4* d = (uint4*)dst;
-  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+  batched<8>(bytes / 16, [&](int i) { return s[i]; }, [&](int i, uint4 v) { d[i] = v; });
 }
 
 __device__ void zero_smem(void* dst, int bytes) {
@@ -165,23 +264,39 @@ __device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int warp, int col) 
   return tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)col;
 }
 
+// Loads the CG bf16 channels of one channel group from global memory.
+template <int CG>
+__device__ __forceinline__ void load_cg(const __nv_bfloat16* p, uint4* v) {
+#pragma unroll
+  for (int k = 0; k < CG / 8; ++k) v[k] = *(const uint4*)(p + 8 * k);
+}
+
+// Epilogue value: ReLU(main * s_m + BN shift) + residual * s_r + bias.
+__device__ __forceinline__ float epi(float m, float r, float sm, float sr, float b2, float rb) {
+  return fmaxf(m * sm + b2, 0.f) + r * sr + rb;
+}
+
 // ---------------------------------------------------------------- encoder
-template <int CI, bool STEM>
-__global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
-  constexpr int CO = 2 * CI, G = CI / 8, NP = CO;
+template <int CI, bool STEM, bool F8>
+__global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
+  using OP = Op<F8>;
+  constexpr int CG = OP::CG, G = CI / CG, CO = 2 * CI, NP = CO;
+  static_assert(!(STEM && F8), "the stem block runs in bf16");
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int nsteps = (CI == 8) ? 5 : 9 * CI / 16;
-  const int in_bytes = STEM ? 3 * (2 * a.band + 6) * (a.w + 6) * 2 : 0;
-  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes);
+  const int nsteps = a.nsteps, T = a.L.terms;
+  const int in_bytes = STEM ? 3 * (2 * a.band + 6) * (a.w + 16) * 2 : 0;
+  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes, T);
+  const size_t lo_off = (size_t)4 * G * a.PIXA * 16;  // low-term planes follow the high-term ones
   Misc M(sm + L.off_misc, CI);
-  __nv_bfloat16* x0 = (__nv_bfloat16*)(sm + L.off_x0);
-  __nv_bfloat16* x1 = (__nv_bfloat16*)(sm + L.off_x1);
+  unsigned char* x0 = sm + L.off_x0;
+  unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.y, band = blockIdx.x, TY = a.band;
   const int h = a.h, w = a.w, ho = h / 2, wo = w / 2;
   const int oy0 = band * TY, WP = a.WP, PIXA = a.PIXA;
+  // 16-byte pixel of plane pl
+  auto px = [&](unsigned char* base, int pl, int p) { return (uint4*)(base + ((size_t)pl * PIXA + p) * 16); };
 
-  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   if (tid == 0) {
     mbar_init(M.bar, 1);
     mbar_fence_init();
@@ -192,55 +307,92 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
   for (int i = tid; i < nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
-  for (int i = tid; i < 8 * CO; i += blockDim.x) M.red[i] = 0.f;
   if (STEM) {
     for (int i = tid; i < 216; i += blockDim.x) M.stw[i] = a.stem_w[i];
     for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
   } else {
-    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.g, M.sa);
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
   }
+  for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
   // 1. block input x into the four phase planes: plane (py, px) holds
   // x[2r + py][2s + px] at local row r - (oy0 - 1), column s + 1.
   const int y_lo = max(0, 2 * oy0 - 2), y_hi = min(h - 1, 2 * oy0 + 2 * TY + 1);
   if (STEM) {
-    const int RI = 2 * TY + 6, CW = w + 6, yi0 = 2 * oy0 - 3;
+    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy0 - 3, nch = CW / 8;
     __nv_bfloat16* sin = (__nv_bfloat16*)(sm + L.off_in);
     const __nv_bfloat16* in = a.in + (size_t)b * 3 * h * w;
-    for (int i = tid; i < 3 * RI * CW; i += blockDim.x) {
-      int c = i / (RI * CW), r = (i / CW) % RI, q = i % CW, y = yi0 + r, x = q - 3;
-      sin[i] = (y >= 0 && y < h && x >= 0 && x < w) ? in[((size_t)c * h + y) * w + x] : __float2bfloat16(0.f);
-    }
+    batched<8>(
+        3 * RI * nch,
+        [&](int i) {
+          int c = i / (RI * nch), r = (i / nch) % RI, x = (i % nch) * 8 - 8, y = yi0 + r;
+          return (y >= 0 && y < h && x >= 0 && x < w) ? *(const uint4*)(in + ((size_t)c * h + y) * w + x)
+                                                      : make_uint4(0, 0, 0, 0);
+        },
+        [&](int i, uint4 v) { *(uint4*)(sin + (size_t)i * 8) = v; });
     __syncthreads();
-    for (int i = tid; i < (y_hi - y_lo + 1) * w; i += blockDim.x) {
-      int y = y_lo + i / w, x = i % w;
-      float acc[8];
+    // stem conv 3 -> 8: two horizontally adjacent positions per thread share
+    // the weight loads
+    const int w2 = w / 2;
+    for (int i = tid; i < (y_hi - y_lo + 1) * w2; i += blockDim.x) {
+      const int y = y_lo + i / w2, x = 2 * (i % w2);
+      float acc0[8], acc1[8];
 #pragma unroll
-      for (int o = 0; o < 8; ++o) acc[o] = M.stb[o];
+      for (int o = 0; o < 8; ++o) acc0[o] = acc1[o] = M.stb[o];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          float v = __bfloat162float(sin[(c * RI + y - yi0 + t / 3 - 1) * CW + x + 3 + t % 3 - 1]);
+        for (int ky = 0; ky < 3; ++ky) {
+          const __nv_bfloat16* row = sin + (c * RI + y - yi0 + ky - 1) * CW + x + 7;
+          float v[4];
 #pragma unroll
-          for (int o = 0; o < 8; ++o) acc[o] += v * M.stw[(c * 9 + t) * 8 + o];
+          for (int q = 0; q < 4; ++q) v[q] = __bfloat162float(row[q]);
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const float4 wa = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8];
+            const float4 wb = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8 + 4];
+            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+              acc0[o] += v[kx] * wv[o];
+              acc1[o] += v[kx + 1] * wv[o];
+            }
+          }
         }
 #pragma unroll
-      for (int o = 0; o < 8; ++o) acc[o] = fmaxf(acc[o], 0.f);
-      int pl = (y & 1) * 2 + (x & 1), p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
-      *(uint4*)(x0 + ((size_t)pl * PIXA + p) * 8) = f32_to_bf16x8(acc);
+      for (int o = 0; o < 8; ++o) {
+        acc0[o] = fmaxf(acc0[o], 0.f);
+        acc1[o] = fmaxf(acc1[o], 0.f);
+      }
+      const int p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1, pl = (y & 1) * 2;
+      store_px<F8>(px(x0, pl, p), acc0, T, lo_off);
+      store_px<F8>(px(x0, pl + 1, p), acc1, T, lo_off);
     }
   } else {
-    const __nv_bfloat16* in = a.in + (size_t)b * h * w * CI;
-    for (int i = tid; i < (y_hi - y_lo + 1) * w * G; i += blockDim.x) {
-      int g = i % G, pos = i / G, y = y_lo + pos / w, x = pos % w;
-      float f[8];
-      bf16x8_to_f32(*(const uint4*)(in + ((size_t)y * w + x) * CI + g * 8), f);
+    // the band's rows are contiguous in NHWC: item i is pixel i / G, group i % G
+    const __nv_bfloat16* in = a.in + ((size_t)b * h + y_lo) * w * CI;
+    const int n = (y_hi - y_lo + 1) * w * G;
+    for (int base = tid; base < n; base += 4 * blockDim.x) {
+      uint4 v[4][CG / 8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) f[c] *= M.sa[g * 8 + c];
-      int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
-      *(uint4*)(x0 + ((size_t)pl * PIXA + p) * 8) = f32_to_bf16x8(f);
+      for (int u = 0; u < 4; ++u) {
+        int i = base + u * blockDim.x;
+        if (i < n) load_cg<CG>(in + (size_t)i * CG, v[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int i = base + u * blockDim.x;
+        if (i >= n) continue;
+        int g = i % G, pos = i / G, y = y_lo + pos / w, x = pos % w;
+        float f[CG];
+#pragma unroll
+        for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(v[u][k], f + 8 * k);
+#pragma unroll
+        for (int c = 0; c < CG; ++c) f[c] *= M.sa[g * CG + c];
+        int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
+        store_px<F8>(px(x0, pl, p), f, T, lo_off);
+      }
     }
   }
   __syncthreads();
@@ -249,25 +401,35 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
     const int y1_lo = max(0, 2 * oy0 - 1), y1_hi = min(h - 1, 2 * oy0 + 2 * TY - 1);
     for (int i = tid; i < (y1_hi - y1_lo + 1) * w * G; i += blockDim.x) {
       int g = i % G, pos = i / G, y = y1_lo + pos / w, x = pos % w;
-      float acc[8];
+      float acc[CG];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = M.dwb[g * 8 + c];
+      for (int c = 0; c < CG; ++c) acc[c] = M.dwb[g * CG + c];
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
         int pl = ((yy & 1) * 2 + (xx & 1)) * G + g, p = ((yy >> 1) - oy0 + 1) * WP + (xx >> 1) + 1;
-        float f[8];
-        bf16x8_to_f32(*(const uint4*)(x0 + ((size_t)pl * PIXA + p) * 8), f);
+        float f[CG];
+        load_px<F8>(px(x0, pl, p), f, T, lo_off);
+        const float4* wt = (const float4*)&M.dw[t * CI + g * CG];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] += M.dw[t * CI + g * 8 + c] * f[c];
+        for (int q = 0; q < CG / 4; ++q) {
+          float4 wv = wt[q];
+          acc[4 * q] += wv.x * f[4 * q];
+          acc[4 * q + 1] += wv.y * f[4 * q + 1];
+          acc[4 * q + 2] += wv.z * f[4 * q + 2];
+          acc[4 * q + 3] += wv.w * f[4 * q + 3];
+        }
       }
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = fmaxf(acc[c], 0.f);
+      for (int c = 0; c < CG; ++c) acc[c] = fmaxf(acc[c], 0.f);
       int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
-      *(uint4*)(x1 + ((size_t)pl * PIXA + p) * 8) = f32_to_bf16x8(acc);
+      store_px<F8>(px(x1, pl, p), acc, T, lo_off);
     }
   }
   fence_proxy_async();
+  // TMEM is taken only now, so that co-resident CTAs stage while this one
+  // waits for columns
+  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -275,8 +437,9 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
   const int m_lo = WP + 1;
   // 3. stage 2 on the tensor cores
   if (tid == 0) {
-    issue_mmas(tmem, M.ks, nsteps, 1, NP, a.ntile, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
-               smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+    issue_mmas<F8>(tmem, M.ks, nsteps, 1, NP, a.ntile, m_lo, WP, PIXA, T, (uint32_t)lo_off,
+                   (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0), smem_u32(sm + L.off_wm),
+                   smem_u32(sm + L.off_wr));
     commit(M.bar);
   }
   const bool ok = mbar_wait(M.bar, 0);
@@ -285,8 +448,8 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
     if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
     mbar_wait(M.bar, 0);  // bounded: let issued MMAs drain before TMEM is freed
   } else {
-    // 4. epilogue: warps w and w + 4 share TMEM lanes; they take alternate tiles
-    for (int i = warp >> 2; i < a.ntile; i += 2) {
+    // 4. epilogue: warps w, w + 4, ... share TMEM lanes; they take alternate tiles
+    for (int i = warp >> 2; i < a.ntile; i += (int)(blockDim.x >> 7)) {
       int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
       int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
       bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
@@ -299,7 +462,10 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
         ld_wait();
         float o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] = valid ? fmaxf(mv[j] + a.b2[c + j], 0.f) + rv[j] + a.rb[c + j] : 0.f;
+        for (int j = 0; j < 16; ++j)
+          o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
+                             a.rb[c + j])
+                       : 0.f;
         if (valid) {
           *(uint4*)(dst + c) = f32_to_bf16x8(o);
           *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
@@ -315,27 +481,29 @@ __global__ void __launch_bounds__(kThreads) k_enc_tc(TcArgs a) {
   float* part = a.part + ((size_t)b * gridDim.x + band) * CO;
   for (int c = tid; c < CO; c += blockDim.x) {
     float s = 0.f;
-    for (int k = 0; k < 8; ++k) s += M.red[k * CO + c];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += M.red[k * CO + c];
     part[c] = s;
   }
 }
 
 // ---------------------------------------------------------------- decoder
-template <int CI, bool SKIP>
-__global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
-  constexpr int CO = CI / 2, G = CI / 8, NP = CO < 16 ? 16 : CO;
+template <int CI, bool SKIP, bool F8>
+__global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
+  using OP = Op<F8>;
+  constexpr int CG = OP::CG, G = CI / CG, CO = CI / 2, NP = CO < 16 ? 16 : CO;
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int nsteps = 4 * CI / 16;  // per output phase
-  const Smem L = smem_layout(4 * nsteps, NP, G, a.PIXA, 0);
+  const int nsteps = a.nsteps, T = a.L.terms;  // K-steps per output phase
+  const Smem L = smem_layout(4 * nsteps, NP, G, a.PIXA, 0, T);
+  const size_t lo_off = (size_t)G * a.PIXA * 16;
   Misc M(sm + L.off_misc, CI);
-  __nv_bfloat16* x0 = (__nv_bfloat16*)(sm + L.off_x0);
-  __nv_bfloat16* x1 = (__nv_bfloat16*)(sm + L.off_x1);
+  unsigned char* x0 = sm + L.off_x0;
+  unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.y, band = blockIdx.x, TA = a.band;
   const int h = a.h, w = a.w, Ho = 2 * h, Wo = 2 * w;
   const int a0 = band * TA, WP = a.WP, PIXA = a.PIXA;
+  auto px = [&](unsigned char* base, int g, int p) { return (uint4*)(base + ((size_t)g * PIXA + p) * 16); };
 
-  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   if (tid == 0) {
     mbar_init(M.bar, 1);
     mbar_fence_init();
@@ -346,33 +514,48 @@ __global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
   for (int i = tid; i < 4 * nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
-  for (int i = tid; i < 8 * CO; i += blockDim.x) M.red[i] = 0.f;
   const float inv_n = 1.f / (float)(h * w);
-  eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.g, M.sa);
-  if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.g, M.ss);
+  eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.red, M.g, M.sa);
+  if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.red, M.g, M.ss);
+  for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
   // 1. x = ECA(A) (+ ECA(skip)) at rows a0 - 2 .. a0 + TA + 1; plane pixel
   // (r - a0 + 2) * WP + (c + 2)
   {
     const int r_lo = max(0, a0 - 2), r_hi = min(h - 1, a0 + TA + 1);
-    const __nv_bfloat16* A = a.in + (size_t)b * h * w * CI;
-    const __nv_bfloat16* S = SKIP ? a.skip + (size_t)b * h * w * CI : nullptr;
-    for (int i = tid; i < (r_hi - r_lo + 1) * w * G; i += blockDim.x) {
-      int g = i % G, pos = i / G, r = r_lo + pos / w, c = pos % w;
-      size_t off = ((size_t)r * w + c) * CI + g * 8;
-      float f[8];
-      bf16x8_to_f32(*(const uint4*)(A + off), f);
+    const __nv_bfloat16* A = a.in + ((size_t)b * h + r_lo) * w * CI;
+    const __nv_bfloat16* S = SKIP ? a.skip + ((size_t)b * h + r_lo) * w * CI : nullptr;
+    const int n = (r_hi - r_lo + 1) * w * G;
+    for (int base = tid; base < n; base += 4 * blockDim.x) {
+      uint4 va[4][CG / 8], vs[4][CG / 8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) f[k] *= M.sa[g * 8 + k];
-      if (SKIP) {
-        float s[8];
-        bf16x8_to_f32(*(const uint4*)(S + off), s);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f[k] += M.ss[g * 8 + k] * s[k];
+      for (int u = 0; u < 4; ++u) {
+        int i = base + u * blockDim.x;
+        if (i < n) {
+          load_cg<CG>(A + (size_t)i * CG, va[u]);
+          if (SKIP) load_cg<CG>(S + (size_t)i * CG, vs[u]);
+        }
       }
-      int p = (r - a0 + 2) * WP + c + 2;
-      *(uint4*)(x0 + ((size_t)g * PIXA + p) * 8) = f32_to_bf16x8(f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int i = base + u * blockDim.x;
+        if (i >= n) continue;
+        int g = i % G, pos = i / G, r = r_lo + pos / w, c = pos % w;
+        float f[CG];
+#pragma unroll
+        for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(va[u][k], f + 8 * k);
+#pragma unroll
+        for (int k = 0; k < CG; ++k) f[k] *= M.sa[g * CG + k];
+        if (SKIP) {
+          float sv[CG];
+#pragma unroll
+          for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(vs[u][k], sv + 8 * k);
+#pragma unroll
+          for (int k = 0; k < CG; ++k) f[k] += M.ss[g * CG + k] * sv[k];
+        }
+        store_px<F8>(px(x0, g, (r - a0 + 2) * WP + c + 2), f, T, lo_off);
+      }
     }
   }
   __syncthreads();
@@ -382,30 +565,39 @@ __global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
     for (int i = tid; i < (r_hi - r_lo + 1) * w * G; i += blockDim.x) {
       int g = i % G, pos = i / G, r = r_lo + pos / w, c = pos % w;
       int p = (r - a0 + 2) * WP + c + 2;
-      float acc[8];
+      float acc[CG];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = M.dwb[g * 8 + k];
+      for (int k = 0; k < CG; ++k) acc[k] = M.dwb[g * CG + k];
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
-        float f[8];
-        bf16x8_to_f32(*(const uint4*)(x0 + ((size_t)g * PIXA + p + (t / 3 - 1) * WP + t % 3 - 1) * 8), f);
+        float f[CG];
+        load_px<F8>(px(x0, g, p + (t / 3 - 1) * WP + t % 3 - 1), f, T, lo_off);
+        const float4* wt = (const float4*)&M.dw[t * CI + g * CG];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += M.dw[t * CI + g * 8 + k] * f[k];
+        for (int q = 0; q < CG / 4; ++q) {
+          float4 wv = wt[q];
+          acc[4 * q] += wv.x * f[4 * q];
+          acc[4 * q + 1] += wv.y * f[4 * q + 1];
+          acc[4 * q + 2] += wv.z * f[4 * q + 2];
+          acc[4 * q + 3] += wv.w * f[4 * q + 3];
+        }
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = fmaxf(acc[k], 0.f);
-      *(uint4*)(x1 + ((size_t)g * PIXA + p) * 8) = f32_to_bf16x8(acc);
+      for (int k = 0; k < CG; ++k) acc[k] = fmaxf(acc[k], 0.f);
+      store_px<F8>(px(x1, g, p), acc, T, lo_off);
     }
   }
   fence_proxy_async();
+  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
   const int m_lo = 2 * WP + 2;
   if (tid == 0) {
-    issue_mmas(tmem, M.ks, nsteps, 4, NP, a.ntile, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
-               smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+    issue_mmas<F8>(tmem, M.ks, nsteps, 4, NP, a.ntile, m_lo, WP, PIXA, T, (uint32_t)lo_off,
+                   (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0), smem_u32(sm + L.off_wm),
+                   smem_u32(sm + L.off_wr));
     commit(M.bar);
   }
   const bool ok = mbar_wait(M.bar, 0);
@@ -414,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
     if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
     mbar_wait(M.bar, 0);  // bounded: let issued MMAs drain before TMEM is freed
   } else {
-    for (int i = warp >> 2; i < a.ntile; i += 2) {
+    for (int i = warp >> 2; i < a.ntile; i += (int)(blockDim.x >> 7)) {
       int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
       int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
       bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
@@ -429,7 +621,10 @@ __global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
           ld8(lane_addr(tmem, warp, (i * 8 + 4 + ph) * NP + cc), rv);
           ld_wait();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) o[j] = valid ? fmaxf(mv[j] + a.b2[cc + j], 0.f) + rv[j] + a.rb[cc + j] : 0.f;
+          for (int j = 0; j < 8; ++j)
+            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
+                               a.b2[cc + j], a.rb[cc + j])
+                         : 0.f;
           if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
 #pragma unroll
           for (int j = 0; j < 8; ++j) warp_sum_to(o[j], &M.red[warp * CO + cc + j]);
@@ -443,7 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_dec_tc(TcArgs a) {
   float* part = a.part + ((size_t)b * gridDim.x + band) * CO;
   for (int c = tid; c < CO; c += blockDim.x) {
     float s = 0.f;
-    for (int k = 0; k < 8; ++k) s += M.red[k * CO + c];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += M.red[k * CO + c];
     part[c] = s;
   }
 }
@@ -456,46 +651,65 @@ uint32_t pow2_cols(int cols) {
 
 int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// K-steps per accumulator: two 16-byte channel groups per MMA (K = 16 bf16
+// or 32 E4M3). With a single channel group per pixel, pairs of taps share a
+// K-step instead.
+int steps_per_acc(int b, bool f8) {
+  const int G = kBlkCin[b] / (f8 ? 16 : 8);
+  if (kBlkEnc[b]) return G == 1 ? 5 : 9 * G / 2;
+  return G == 1 ? 2 : 4 * G / 2;
+}
+
 // Band geometry of one level: the largest band (8, 4, 2 or 1 rows) whose
-// accumulators fit the 512 TMEM columns and whose planes fit shared memory.
+// accumulators fit the TMEM columns and whose planes fit shared memory.
+// Two passes: first a band that lets two CTAs share an SM (shared memory
+// <= half, TMEM <= 256 columns), then any band that fits.
 struct Geo {
-  int band, ntile, WP, PIXA, smem;
+  int band, ntile, WP, PIXA, smem, threads;
   uint32_t cols;
 };
 
-Geo encoder_geo(int CI, bool stem, int h, int w) {
-  const int CO = 2 * CI, G = CI / 8, wo = w / 2, nsteps = CI == 8 ? 5 : 9 * CI / 16;
+Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
+  const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
+  const bool stem = b == 0;
   Geo g{};
-  for (int TY = 8; TY >= 1; TY >>= 1) {
-    g.band = TY;
-    g.WP = wo + 2;
-    int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
-    g.ntile = cdiv(count, 128);
-    g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
-    g.PIXA = (g.PIXA + 7) / 8 * 8;
-    int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 6) * 2 : 0;
-    g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes).total;
-    g.cols = pow2_cols(g.ntile * 2 * CO);
-    if (g.ntile * 2 * CO <= 512 && g.smem <= kTcMaxSmem) return g;
-  }
+  for (int pass = 0; pass < 2; ++pass)
+    for (int TY = 8; TY >= 1; TY >>= 1) {
+      g.band = TY;
+      g.WP = wo + 2;
+      int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
+      g.ntile = cdiv(count, 128);
+      g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
+      g.PIXA = (g.PIXA + 7) / 8 * 8;
+      int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
+      g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms).total;
+      g.cols = pow2_cols(g.ntile * 2 * CO);
+      g.threads = pass == 0 ? 256 : 512;
+      if (pass == 0 ? (g.cols <= 256 && g.smem <= kTcHalfSmem) : (g.ntile * 2 * CO <= 512 && g.smem <= kTcMaxSmem))
+        return g;
+    }
   g.band = 0;
   return g;
 }
 
-Geo decoder_geo(int CI, int h, int w) {
-  const int CO = CI / 2, G = CI / 8, NP = CO < 16 ? 16 : CO, nsteps = 4 * CI / 16;
+Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
+  const int CI = kBlkCin[b], CO = CI / 2, G = CI / (f8 ? 16 : 8), NP = CO < 16 ? 16 : CO,
+            nsteps = steps_per_acc(b, f8);
   Geo g{};
-  for (int TA = 8; TA >= 1; TA >>= 1) {
-    g.band = TA;
-    g.WP = w + 4;
-    int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
-    g.ntile = cdiv(count, 128);
-    g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
-    g.PIXA = (g.PIXA + 7) / 8 * 8;
-    g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0).total;
-    g.cols = pow2_cols(g.ntile * 8 * NP);
-    if (g.ntile * 8 * NP <= 512 && g.smem <= kTcMaxSmem) return g;
-  }
+  for (int pass = 0; pass < 2; ++pass)
+    for (int TA = 8; TA >= 1; TA >>= 1) {
+      g.band = TA;
+      g.WP = w + 4;
+      int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
+      g.ntile = cdiv(count, 128);
+      g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
+      g.PIXA = (g.PIXA + 7) / 8 * 8;
+      g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0, terms).total;
+      g.cols = pow2_cols(g.ntile * 8 * NP);
+      g.threads = pass == 0 ? 256 : 512;
+      if (pass == 0 ? (g.cols <= 256 && g.smem <= kTcHalfSmem) : (g.ntile * 8 * NP <= 512 && g.smem <= kTcMaxSmem))
+        return g;
+    }
   g.band = 0;
   return g;
 }
@@ -504,7 +718,7 @@ template <typename K>
 cudaError_t launch(K kern, const Geo& g, int B, const TcArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
   if (e) return e;
-  kern<<<dim3(a.tiles_per_window, B), kThreads, g.smem, st>>>(a);
+  kern<<<dim3(a.tiles_per_window, B), g.threads, g.smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -519,87 +733,127 @@ int tap_phase(int k) { return k == 1 ? 0 : 1; }
 int tap_shift(int k) { return k == 0 ? -1 : 0; }
 }  // namespace
 
-void pack_tc(const float* folded, const FoldedOffsets& off, std::vector<unsigned char>* blob, TcPackOffsets* po) {
-  std::vector<__nv_bfloat16> w;
+void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int f8_terms,
+             std::vector<unsigned char>* blob, TcPackOffsets* po) {
+  std::vector<unsigned char> w;  // packed operands, then scales, then K-step tables
+  std::vector<float> scales;
   std::vector<KStep> ks_all;
-  std::vector<size_t> ks_start(6);
-  size_t wm_elems[6], wr_elems[6];
+  size_t ks_start[6], sc_start[6][2];
+  auto align128 = [&]() {
+    while (w.size() % 128) w.push_back(0);
+  };
   for (int b = 0; b < kNumBlocks; ++b) {
-    const int ci = kBlkCin[b], co = kBlkCout[b], G = ci / 8;
+    const int ci = kBlkCin[b], co = kBlkCout[b], CG = f8[b] ? 16 : 8, G = ci / CG;
     const bool enc = kBlkEnc[b];
     const int NP = enc ? co : (co < 16 ? 16 : co);
-    std::vector<KStep> ks;
-    // each K-step: two (tap, channel group) halves; weights w(tap, ci, co)
     struct Half {
       int tap, g;  // tap < 0: zero half
     };
+    std::vector<KStep> ks;
     std::vector<std::pair<Half, Half>> halves;
+    auto add = [&](int tap0, int g0, int pl0, int dr0, int dc0, int tap1, int g1, int pl1, int dr1, int dc1) {
+      ks.push_back({(int8_t)pl0, (int8_t)dr0, (int8_t)dc0, (int8_t)pl1, (int8_t)dr1, (int8_t)dc1, 0, 0});
+      halves.push_back({{tap0, g0}, {tap1, g1}});
+    };
     if (enc) {
-      auto tap_ks = [&](int t, int g) {
-        int ky = t / 3, kx = t % 3;
-        return std::make_tuple((tap_phase(ky) * 2 + tap_phase(kx)) * G + g, tap_shift(ky), tap_shift(kx));
-      };
-      if (ci == 8) {
+      auto plane = [&](int t, int g) { return (tap_phase(t / 3) * 2 + tap_phase(t % 3)) * G + g; };
+      if (G == 1) {
+        // pairs of taps in the same phase plane, second half at a larger address
         const int pairs[5][2] = {{0, 2}, {6, 8}, {1, 7}, {3, 5}, {4, -1}};
         for (auto& pr : pairs) {
-          auto [p0, r0, c0] = tap_ks(pr[0], 0);
-          KStep k{(int8_t)p0, (int8_t)r0, (int8_t)c0, (int8_t)p0, (int8_t)r0, (int8_t)(c0 + 1), 0, 0};
-          if (pr[1] >= 0) {
-            auto [p1, r1, c1] = tap_ks(pr[1], 0);
-            k.pl1 = (int8_t)p1;
-            k.dr1 = (int8_t)r1;
-            k.dc1 = (int8_t)c1;
-          }
-          ks.push_back(k);
-          halves.push_back({{pr[0], 0}, {pr[1], 0}});
+          int t0 = pr[0], t1 = pr[1];
+          if (t1 >= 0)
+            add(t0, 0, plane(t0, 0), tap_shift(t0 / 3), tap_shift(t0 % 3), t1, 0, plane(t1, 0), tap_shift(t1 / 3),
+                tap_shift(t1 % 3));
+          else
+            add(t0, 0, plane(t0, 0), tap_shift(t0 / 3), tap_shift(t0 % 3), -1, 0, plane(t0, 0), tap_shift(t0 / 3),
+                tap_shift(t0 % 3) + 1);
         }
       } else {
         for (int t = 0; t < 9; ++t)
-          for (int kg = 0; kg < G / 2; ++kg) {
-            auto [p0, r0, c0] = tap_ks(t, 2 * kg);
-            ks.push_back({(int8_t)p0, (int8_t)r0, (int8_t)c0, (int8_t)(p0 + 1), (int8_t)r0, (int8_t)c0, 0, 0});
-            halves.push_back({{t, 2 * kg}, {t, 2 * kg + 1}});
-          }
+          for (int kg = 0; kg < G / 2; ++kg)
+            add(t, 2 * kg, plane(t, 2 * kg), tap_shift(t / 3), tap_shift(t % 3), t, 2 * kg + 1, plane(t, 2 * kg + 1),
+                tap_shift(t / 3), tap_shift(t % 3));
       }
     } else {
       for (int ph = 0; ph < 4; ++ph) {
-        int py = ph >> 1, px = ph & 1;
-        for (int st = 0; st < 4; ++st)
-          for (int kg = 0; kg < G / 2; ++kg) {
-            int dy = (st >> 1) - 1 + py, dx = (st & 1) - 1 + px;
-            ks.push_back({(int8_t)(2 * kg), (int8_t)dy, (int8_t)dx, (int8_t)(2 * kg + 1), (int8_t)dy, (int8_t)dx, 0,
-                          0});
-            halves.push_back({{ph * 4 + st, 2 * kg}, {ph * 4 + st, 2 * kg + 1}});
-          }
+        const int py = ph >> 1, px = ph & 1;
+        auto dy = [&](int st) { return (st >> 1) - 1 + py; };
+        auto dx = [&](int st) { return (st & 1) - 1 + px; };
+        if (G == 1) {
+          for (int st = 0; st < 4; st += 2)  // sub-taps (sy, 0) and (sy, 1): one column apart
+            add(ph * 4 + st, 0, 0, dy(st), dx(st), ph * 4 + st + 1, 0, 0, dy(st + 1), dx(st + 1));
+        } else {
+          for (int st = 0; st < 4; ++st)
+            for (int kg = 0; kg < G / 2; ++kg)
+              add(ph * 4 + st, 2 * kg, 2 * kg, dy(st), dx(st), ph * 4 + st, 2 * kg + 1, 2 * kg + 1, dy(st), dx(st));
+        }
       }
     }
-    // packed [step][half][n < NP][8]
     for (int br = 0; br < 2; ++br) {
       const float* src = folded + (br == 0 ? off.w2[b] : off.rw[b]);
-      (br == 0 ? wm_elems[b] : wr_elems[b]) = w.size();
-      for (auto& hh : halves)
-        for (int hf = 0; hf < 2; ++hf) {
-          Half h = hf == 0 ? hh.first : hh.second;
-          for (int n = 0; n < NP; ++n)
-            for (int c = 0; c < 8; ++c) {
-              float v = 0.f;
-              if (h.tap >= 0 && n < co) v = src[((size_t)h.tap * ci + h.g * 8 + c) * co + n];
-              w.push_back(__float2bfloat16(v));
-            }
+      auto wt = [&](const Half& h, int n, int c) {
+        return (h.tap >= 0 && n < co) ? src[((size_t)h.tap * ci + h.g * CG + c) * co + n] : 0.f;
+      };
+      // per output channel scale (E4M3): max |w| / 448
+      std::vector<float> sc(NP, 1.f);
+      if (f8[b]) {
+        for (int n = 0; n < NP; ++n) {
+          float m = 0.f;
+          for (auto& hh : halves)
+            for (int c = 0; c < CG; ++c) m = std::max(m, std::max(std::fabs(wt(hh.first, n, c)), std::fabs(wt(hh.second, n, c))));
+          sc[n] = m > 0.f ? m / 448.f : 1.f;
         }
-      while (w.size() % 64) w.push_back(__float2bfloat16(0.f));  // 128-byte alignment
+      }
+      align128();
+      (br == 0 ? po->wm[b] : po->wr[b]) = w.size();
+      // [term][step][half][n < NP][CG] elements, 16 bytes per (half, n); the
+      // E4M3 low term holds the rounding remainder of the high term
+      const int T = f8[b] ? f8_terms : 1;
+      for (int term = 0; term < T; ++term)
+        for (auto& hh : halves)
+          for (int hf = 0; hf < 2; ++hf) {
+            const Half& h = hf == 0 ? hh.first : hh.second;
+            for (int n = 0; n < NP; ++n)
+              for (int c = 0; c < CG; ++c) {
+                float v = wt(h, n, c);
+                if (f8[b]) {
+                  float x = v / sc[n];
+                  __nv_fp8_storage_t hi = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+                  if (term == 1) {
+                    float hf_ = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
+                    hi = __nv_cvt_float_to_fp8(x - hf_, __NV_SATFINITE, __NV_E4M3);
+                  }
+                  w.push_back((unsigned char)hi);
+                } else {
+                  __nv_bfloat16 q = __float2bfloat16(v);
+                  unsigned char bytes[2];
+                  std::memcpy(bytes, &q, 2);
+                  w.push_back(bytes[0]);
+                  w.push_back(bytes[1]);
+                }
+              }
+          }
+      sc_start[b][br] = scales.size();
+      scales.insert(scales.end(), sc.begin(), sc.end());
     }
     ks_start[b] = ks_all.size();
     ks_all.insert(ks_all.end(), ks.begin(), ks.end());
   }
-  size_t wbytes = w.size() * sizeof(__nv_bfloat16);
-  blob->assign(wbytes + ks_all.size() * sizeof(KStep), 0);
-  std::memcpy(blob->data(), w.data(), wbytes);
-  std::memcpy(blob->data() + wbytes, ks_all.data(), ks_all.size() * sizeof(KStep));
+  align128();
+  size_t sc_off = w.size();
+  size_t ks_off = sc_off + (scales.size() * sizeof(float) + 127) / 128 * 128;
+  blob->assign(ks_off + ks_all.size() * sizeof(KStep), 0);
+  std::memcpy(blob->data(), w.data(), w.size());
+  std::memcpy(blob->data() + sc_off, scales.data(), scales.size() * sizeof(float));
+  std::memcpy(blob->data() + ks_off, ks_all.data(), ks_all.size() * sizeof(KStep));
   for (int b = 0; b < kNumBlocks; ++b) {
-    po->wm[b] = wm_elems[b] * sizeof(__nv_bfloat16);
-    po->wr[b] = wr_elems[b] * sizeof(__nv_bfloat16);
-    po->ks[b] = wbytes + ks_start[b] * sizeof(KStep);
+    po->ks[b] = ks_off + ks_start[b] * sizeof(KStep);
+    po->swm[b] = sc_off + sc_start[b][0] * sizeof(float);
+    po->swr[b] = sc_off + sc_start[b][1] * sizeof(float);
+    po->f8[b] = f8[b];
+    po->terms[b] = f8[b] ? f8_terms : 1;
+    po->nsteps[b] = steps_per_acc(b, f8[b]);
   }
   po->total = blob->size();
 }
@@ -607,8 +861,9 @@ void pack_tc(const float* folded, const FoldedOffsets& off, std::vector<unsigned
 TcWeights tc_weights_from(const unsigned char* base, const TcPackOffsets& po) {
   TcWeights t;
   for (int b = 0; b < kNumBlocks; ++b)
-    t.layer[b] = TcLayer{(const __nv_bfloat16*)(base + po.wm[b]), (const __nv_bfloat16*)(base + po.wr[b]),
-                         (const KStep*)(base + po.ks[b])};
+    t.layer[b] = TcLayer{base + po.wm[b], base + po.wr[b], (const KStep*)(base + po.ks[b]),
+                         (const float*)(base + po.swm[b]), (const float*)(base + po.swr[b]), po.f8[b],
+                         po.terms[b], po.nsteps[b]};
   return t;
 }
 
@@ -619,10 +874,11 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
   int tiles[6];
   const void* prev = nullptr;
   for (int l = 0; l < 6; ++l) {
-    const int ci = kBlkCin[l];
     static const int in_div[6] = {1, 2, 4, 8, 4, 2};
     const int h = H / in_div[l], wd = W / in_div[l];
-    Geo g = kBlkEnc[l] ? encoder_geo(ci, l == 0, h, wd) : decoder_geo(ci, h, wd);
+    const bool f8 = tw.layer[l].f8;
+    const int terms = tw.layer[l].terms;
+    Geo g = kBlkEnc[l] ? encoder_geo(l, f8, terms, h, wd) : decoder_geo(l, f8, terms, h, wd);
     if (g.band == 0) return cudaErrorInvalidConfiguration;
     TcArgs a{};
     a.in = (const __nv_bfloat16*)(l == 0 ? (const void*)in : prev);
@@ -652,6 +908,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.b2 = w.blk[l].b2;
     a.rb = w.blk[l].rb;
     a.L = tw.layer[l];
+    a.nsteps = tw.layer[l].nsteps;
     a.out = (__nv_bfloat16*)s.act[l];
     a.part = s.part[l];
     a.status = status;
@@ -659,13 +916,19 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.tiles_per_window = cdiv(rows, g.band);
     tiles[l] = a.tiles_per_window;
     hook->begin(K_ENC1 + l, st);
-    switch (l) {
-      case 0: e = launch(k_enc_tc<8, true>, g, B, a, st); break;
-      case 1: e = launch(k_enc_tc<16, false>, g, B, a, st); break;
-      case 2: e = launch(k_enc_tc<32, false>, g, B, a, st); break;
-      case 3: e = launch(k_dec_tc<64, false>, g, B, a, st); break;
-      case 4: e = launch(k_dec_tc<32, true>, g, B, a, st); break;
-      case 5: e = launch(k_dec_tc<16, true>, g, B, a, st); break;
+    switch (l * 2 + (f8 ? 1 : 0)) {
+      case 0: e = launch(k_enc_tc<8, true, false>, g, B, a, st); break;
+      case 2: e = launch(k_enc_tc<16, false, false>, g, B, a, st); break;
+      case 3: e = launch(k_enc_tc<16, false, true>, g, B, a, st); break;
+      case 4: e = launch(k_enc_tc<32, false, false>, g, B, a, st); break;
+      case 5: e = launch(k_enc_tc<32, false, true>, g, B, a, st); break;
+      case 6: e = launch(k_dec_tc<64, false, false>, g, B, a, st); break;
+      case 7: e = launch(k_dec_tc<64, false, true>, g, B, a, st); break;
+      case 8: e = launch(k_dec_tc<32, true, false>, g, B, a, st); break;
+      case 9: e = launch(k_dec_tc<32, true, true>, g, B, a, st); break;
+      case 10: e = launch(k_dec_tc<16, true, false>, g, B, a, st); break;
+      case 11: e = launch(k_dec_tc<16, true, true>, g, B, a, st); break;
+      default: e = cudaErrorInvalidConfiguration;
     }
     hook->end(st);
     if (e) return e;

@@ -20,16 +20,22 @@ struct KStep {
 // order, [accumulator phase][K-step][K half][N padded][8] bf16, and the
 // K-step table ([phase][K-step]).
 struct TcLayer {
-  const __nv_bfloat16* wm;
-  const __nv_bfloat16* wr;
+  const unsigned char* wm;
+  const unsigned char* wr;
   const KStep* ks;
+  const float* swm;  // E4M3 per-output-channel weight scales (main, residual)
+  const float* swr;
+  bool f8;           // E4M3 operands (kind::f8f6f4) instead of bf16
+  int terms;         // E4M3 terms per operand: 1, or 2 (high + rounding remainder)
+  int nsteps;        // K-steps per accumulator
 };
 struct TcWeights {
   TcLayer layer[6];
 };
 
-constexpr int kTcMiscBytes = 7424;
+constexpr int kTcMiscBytes = 9344;
 constexpr int kTcMaxSmem = 227 * 1024;
+constexpr int kTcHalfSmem = 113 * 1024;  // two CTAs per SM
 
 struct TcArgs {
   const __nv_bfloat16* in;  // block 1: raw frames [B][3][H][W]; else previous block [B][h][w][CI]
@@ -45,6 +51,7 @@ struct TcArgs {
   int ntile;      // 128-row GEMM tiles per CTA
   int WP, PIXA;   // plane pitch and pixels per plane
   int tiles_per_window;
+  int nsteps;
   uint32_t tmem_cols;
   const float *stem_w, *stem_b, *dw, *dwb, *b2, *rb;
   TcLayer L;
@@ -56,11 +63,16 @@ struct TcArgs {
 // Host: packs the folded FP32 weights of every block for the tensor cores.
 // Returns byte offsets (into one device buffer) of each block's tensors.
 struct TcPackOffsets {
-  size_t wm[6], wr[6], ks[6];
+  size_t wm[6], wr[6], ks[6], swm[6], swr[6];
+  bool f8[6];
+  int terms[6];
+  int nsteps[6];
   size_t total;
 };
-void pack_tc(const float* folded, const FoldedOffsets& off, std::vector<unsigned char>* blob,
-             TcPackOffsets* po);
+// f8[b]: block b's stage-2 operands in E4M3 (needs 16 or more input
+// channels), with f8_terms (1 or 2) E4M3 terms per operand.
+void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int f8_terms,
+             std::vector<unsigned char>* blob, TcPackOffsets* po);
 TcWeights tc_weights_from(const unsigned char* dev_base, const TcPackOffsets& po);
 
 // Forward of the six blocks on the tensor cores (output conv excluded);

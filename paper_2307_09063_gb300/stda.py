@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstda.so")
 
 OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_UNSUPPORTED, WARMUP = range(9)
-FP32, BF16, FP8_E4M3 = 0, 1, 2
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8_E4M3}
+FP32, BF16, FP8_E4M3, FP8_E4M3_FAST = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8_E4M3, "fp8_fast": FP8_E4M3_FAST}
 MAX_TGT = 16
 
 

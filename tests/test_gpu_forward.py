@@ -131,6 +131,49 @@ def test_bf16_tensor_core_matches_cuda_core_path(stda, monkeypatch):
     assert (tc - simt).abs().max().item() <= BF16_ATOL
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 24, 40), (1, 8, 8), (2, 72, 136), (1, 256, 128), (1, 512, 256)])
+def test_fp8_tensor_core_forward_shapes(stda, weights, B, H, W):
+    """E4M3 stage-2 operands (blocks 2-6, two E4M3 terms per operand; block 1
+    in bf16) against the oracle, at the BF16 bound."""
+    rng = np.random.default_rng(H * 11 + W)
+    x = bf16_round(rng.uniform(0, 1, (B, 3, H, W)))
+    ref = O.forward_batch(*weights, x)
+    xd = torch.from_numpy(x).cuda().to(torch.bfloat16)
+    ctx = stda.Context(H, W, B, "fp8", 0)
+    got = ctx.forward(xd)[:, 0].float().cpu().numpy()
+    assert ctx.device_status() == stda.OK
+    err = np.max(np.abs(got - ref))
+    fast = stda.Context(H, W, B, "fp8_fast", 0).forward(xd)[:, 0].float().cpu().numpy()
+    err_fast = np.max(np.abs(fast - ref))
+    print(f"fp8 {H}x{W}: max abs err two-term {err:.4f}, one-term {err_fast:.4f}")
+    assert err <= BF16_ATOL
+    assert np.all(np.isfinite(fast)) and err_fast < 0.5
+
+
+def test_fp8_forward_full_batch_512x256(stda, weights):
+    """1024 windows of 3 x 512 x 256 in the E4M3 path, 8 sampled windows
+    against the oracle and, at output SINR, against the plain FP32 path."""
+    w = I.WORKLOADS[4]
+    g = w.gen
+    noisy, _, bins, ntgt = stda.generate(g, 0, w.cid, 0, w.batch, dtype=torch.bfloat16, with_clean=False)
+    ctx = stda.Context(g.P, g.Q, w.batch, "fp8", 0)
+    out = ctx.forward(noisy)
+    assert ctx.device_status() == stda.OK
+    ctx32 = stda.Context(g.P, g.Q, 1, "fp32", 0)
+    ctxb = stda.Context(g.P, g.Q, 1, "bf16", 0)
+    torch.cuda.synchronize()
+    for k in I.parity_windows(w.batch):
+        onoisy, _, obins = O.gen_window(0, w.cid, k, g, with_clean=False)
+        assert np.array_equal(bins[k, :ntgt[k]].cpu().numpy(), obins)
+        ref = O.forward(*weights, bf16_round(onoisy))
+        got = out[k, 0].float().cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= BF16_ATOL
+        z32 = ctx32.forward(noisy[k:k + 1].float().contiguous())[0, 0].cpu().numpy()
+        zb = ctxb.forward(noisy[k:k + 1].contiguous())[0, 0].float().cpu().numpy()
+        assert abs(_sinr(got, obins) - _sinr(z32, obins)) <= SINR_DB_TOL
+        assert abs(_sinr(got, obins) - _sinr(zb, obins)) <= SINR_DB_TOL
+
+
 def test_invalid_calls_return_status(stda):
     ctx = stda.Context(32, 32, 2, "fp32", 0)
     x = torch.zeros((2, 3, 32, 32), device="cuda")
