@@ -99,10 +99,10 @@ def lib():
             L.orc_sinr_db.argtypes = [_D, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int]
             L.orc_evm.restype = ctypes.c_double
             L.orc_evm.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int]
-            if hasattr(L, "orc_loss_grad"):
-                L.orc_loss_grad.restype = ctypes.c_double
-                L.orc_loss_grad.argtypes = [_F, _F, _F, _F, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D,
-                                            ctypes.c_int]
+            L.orc_loss_grad.restype = ctypes.c_double
+            L.orc_loss_grad.argtypes = [_F, _F, _F, _F, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int]
+            L.orc_adjoint.restype = ctypes.c_int
+            L.orc_adjoint.argtypes = [_F, _F, _F, _D, ctypes.c_int, ctypes.c_int, _D, _D]
             _lib = L
     return _lib
 
@@ -258,6 +258,28 @@ def eca(m, k3):
     k3 = _f64(k3)
     lib().orc_eca(_p(m, _D), C, h, w, _p(k3, _D))
     return m
+
+
+def adjoint(params, buffers, x, gout):
+    """(dL/dtheta [num_params], dL/dx [3][H][W]) of one window given dL/dz."""
+    params, buffers, x = _f32(params), _f32(buffers), _f32(x)
+    _, H, W = x.shape
+    g = _f64(gout)
+    gp = np.empty(num_params())
+    gi = np.empty((3, H, W))
+    if lib().orc_adjoint(_p(params, _F), _p(buffers, _F), _p(x, _F), _p(g, _D), H, W, _p(gp, _D), _p(gi, _D)):
+        raise ValueError("oracle adjoint rejected the shape")
+    return gp, gi
+
+
+def loss_grad(params, buffers, x, target, nthreads=None):
+    """(MSE loss, dL/dtheta) over a batch x[B][3][H][W], target[B][H][W]."""
+    params, buffers, x, t = _f32(params), _f32(buffers), _f32(x), _f32(target)
+    B, _, H, W = x.shape
+    gp = np.empty(num_params())
+    loss = lib().orc_loss_grad(_p(params, _F), _p(buffers, _F), _p(x, _F), _p(t, _F), B, H, W, _p(gp, _D),
+                               nthreads or os.cpu_count() or 1)
+    return loss, gp
 
 
 # ------------------------------------------------------------------ metrics

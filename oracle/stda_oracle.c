@@ -661,6 +661,411 @@ int orc_forward_batch(const float* params, const float* buffers,
 }
 
 /* ======================================================================== */
+/* Gradient (adjoint of the forward pass), FP64.                            */
+/* ======================================================================== */
+
+/* Adjoints of the primitives, direct sums (accumulate into dx / dw / db). */
+static void conv2d_bwd(const double* x, int Ci, int H, int W, const double* w, int Co, int k, int stride,
+                       int pad, int groups, const double* dy, double* dx, double* dw, double* db) {
+  int Ho = (H + 2 * pad - k) / stride + 1;
+  int Wo = (W + 2 * pad - k) / stride + 1;
+  int cig = Ci / groups, cog = Co / groups;
+  for (int o = 0; o < Co; ++o) {
+    int g = o / cog;
+    for (int Y = 0; Y < Ho; ++Y)
+      for (int X = 0; X < Wo; ++X) {
+        double d = dy[((size_t)o * Ho + Y) * Wo + X];
+        if (db) db[o] += d;
+        for (int il = 0; il < cig; ++il) {
+          int i = g * cig + il;
+          for (int ky = 0; ky < k; ++ky) {
+            int yy = Y * stride - pad + ky;
+            if (yy < 0 || yy >= H) continue;
+            for (int kx = 0; kx < k; ++kx) {
+              int xx = X * stride - pad + kx;
+              if (xx < 0 || xx >= W) continue;
+              size_t wi = (((size_t)o * cig + il) * k + ky) * k + kx;
+              size_t xi = ((size_t)i * H + yy) * W + xx;
+              if (dw) dw[wi] += d * x[xi];
+              if (dx) dx[xi] += d * w[wi];
+            }
+          }
+        }
+      }
+  }
+}
+
+static void conv_transpose2d_bwd(const double* x, int Ci, int H, int W, const double* w, int Co, int k,
+                                 int stride, int pad, int groups, const double* dy, double* dx, double* dw,
+                                 double* db) {
+  int Ho = (H - 1) * stride - 2 * pad + k;
+  int Wo = (W - 1) * stride - 2 * pad + k;
+  int cig = Ci / groups, cog = Co / groups;
+  if (db)
+    for (int o = 0; o < Co; ++o)
+      for (int t = 0; t < Ho * Wo; ++t) db[o] += dy[(size_t)o * Ho * Wo + t];
+  for (int i = 0; i < Ci; ++i) {
+    int g = i / cig;
+    for (int yi = 0; yi < H; ++yi)
+      for (int xi = 0; xi < W; ++xi) {
+        size_t xo = ((size_t)i * H + yi) * W + xi;
+        for (int ol = 0; ol < cog; ++ol) {
+          int o = g * cog + ol;
+          for (int ky = 0; ky < k; ++ky) {
+            int Y = yi * stride - pad + ky;
+            if (Y < 0 || Y >= Ho) continue;
+            for (int kx = 0; kx < k; ++kx) {
+              int X = xi * stride - pad + kx;
+              if (X < 0 || X >= Wo) continue;
+              double d = dy[((size_t)o * Ho + Y) * Wo + X];
+              size_t wi = (((size_t)i * cog + ol) * k + ky) * k + kx;
+              if (dw) dw[wi] += d * x[xo];
+              if (dx) dx[xo] += d * w[wi];
+            }
+          }
+        }
+      }
+  }
+}
+
+/* BN in inference form: y = gam (x - mean) / sqrt(var + eps) + bet. Given dy,
+ * accumulates dgam, dbet and (if dx) dx. */
+static void batchnorm_bwd(const double* x, int C, int n, const double* gam, const double* mean,
+                          const double* var, const double* dy, double* dx, double* dgam, double* dbet) {
+  for (int c = 0; c < C; ++c) {
+    double is = 1.0 / sqrt(var[c] + BN_EPS);
+    for (int t = 0; t < n; ++t) {
+      double d = dy[(size_t)c * n + t];
+      dgam[c] += d * (x[(size_t)c * n + t] - mean[c]) * is;
+      dbet[c] += d;
+      if (dx) dx[(size_t)c * n + t] += d * gam[c] * is;
+    }
+  }
+}
+
+/* Saved tensors of one block (for the adjoint). */
+typedef struct {
+  int h, w, H2, W2;
+  double *x, *t1, *t2, *x1, *u, *y, *g, *s;
+} blk_tape;
+
+/* Gradient pointers of one block, in the canonical blob. */
+typedef struct {
+  double *w1, *g1, *b1, *w3, *g2, *b2, *g3, *b3, *w2, *g, *b, *rw, *rb, *eca;
+} blk_grad;
+
+static double* dup(const double* a, size_t n) {
+  double* r = malloc(sizeof(double) * n);
+  memcpy(r, a, sizeof(double) * n);
+  return r;
+}
+
+/* Forward of one block keeping its intermediates (same arithmetic as
+ * block_forward). Returns the post-ECA output. */
+static double* block_forward_tape(const orc_blk* k, const double* x, int h, int w, blk_tape* T) {
+  int ci = k->cin, co = k->cout;
+  size_t n = (size_t)h * w;
+  T->h = h;
+  T->w = w;
+  T->x = dup(x, ci * n);
+  T->t1 = malloc(sizeof(double) * ci * n);
+  T->t2 = malloc(sizeof(double) * ci * n);
+  if (k->enc) {
+    orc_conv2d(x, ci, h, w, k->w1, NULL, ci, 1, 1, 0, ci, T->t1);
+    orc_conv2d(x, ci, h, w, k->w3, NULL, ci, 3, 1, 1, ci, T->t2);
+  } else {
+    orc_conv_transpose2d(x, ci, h, w, k->w1, NULL, ci, 1, 1, 0, ci, T->t1);
+    orc_conv_transpose2d(x, ci, h, w, k->w3, NULL, ci, 3, 1, 1, ci, T->t2);
+  }
+  double* b1 = dup(T->t1, ci * n);
+  double* b2 = dup(T->t2, ci * n);
+  double* b3 = dup(x, ci * n);
+  batchnorm(b1, ci, (int)n, k->g1, k->b1, k->m1, k->v1);
+  batchnorm(b2, ci, (int)n, k->g2, k->b2, k->m2, k->v2);
+  batchnorm(b3, ci, (int)n, k->g3, k->b3, k->m3, k->v3);
+  T->x1 = malloc(sizeof(double) * ci * n);
+  for (size_t t = 0; t < ci * n; ++t) T->x1[t] = b1[t] + b2[t] + b3[t];
+  relu(T->x1, ci * n);
+  free(b1); free(b2); free(b3);
+  int H2 = k->enc ? h / 2 : 2 * h, W2 = k->enc ? w / 2 : 2 * w;
+  size_t n2 = (size_t)H2 * W2;
+  T->H2 = H2;
+  T->W2 = W2;
+  T->u = malloc(sizeof(double) * co * n2);
+  double* rs = malloc(sizeof(double) * co * n2);
+  if (k->enc) {
+    orc_conv2d(T->x1, ci, h, w, k->w2, NULL, co, 3, 2, 1, 1, T->u);
+    orc_conv2d(x, ci, h, w, k->rw, k->rb, co, 3, 2, 1, 1, rs);
+  } else {
+    orc_conv_transpose2d(T->x1, ci, h, w, k->w2, NULL, co, 4, 2, 1, 1, T->u);
+    orc_conv_transpose2d(x, ci, h, w, k->rw, k->rb, co, 4, 2, 1, 1, rs);
+  }
+  T->y = dup(T->u, co * n2);
+  batchnorm(T->y, co, (int)n2, k->g, k->b, k->m, k->v);
+  relu(T->y, co * n2);
+  for (size_t t = 0; t < co * n2; ++t) T->y[t] += rs[t];
+  free(rs);
+  /* ECA, keeping g and s */
+  T->g = malloc(sizeof(double) * co);
+  T->s = malloc(sizeof(double) * co);
+  for (int c = 0; c < co; ++c) {
+    double a = 0.0;
+    for (size_t t = 0; t < n2; ++t) a += T->y[c * n2 + t];
+    T->g[c] = a / (double)n2;
+  }
+  double* out = malloc(sizeof(double) * co * n2);
+  for (int c = 0; c < co; ++c) {
+    double z = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      int cc = c + j - 1;
+      if (cc >= 0 && cc < co) z += k->eca[j] * T->g[cc];
+    }
+    T->s[c] = 1.0 / (1.0 + exp(-z));
+    for (size_t t = 0; t < n2; ++t) out[c * n2 + t] = T->s[c] * T->y[c * n2 + t];
+  }
+  return out;
+}
+
+/* Adjoint of one block: dout (gradient of the post-ECA output) -> dx
+ * (gradient of the block input, accumulated) and the parameter gradients. */
+static void block_backward(const orc_blk* k, const blk_tape* T, const double* dout, double* dx, blk_grad* G) {
+  int ci = k->cin, co = k->cout, h = T->h, w = T->w, H2 = T->H2, W2 = T->W2;
+  size_t n = (size_t)h * w, n2 = (size_t)H2 * W2;
+  /* ECA: out = s * y, s = sigmoid(z), z = conv1d(g), g = mean(y) */
+  double* dy = malloc(sizeof(double) * co * n2);
+  double* dz = calloc(co, sizeof(double));
+  for (int c = 0; c < co; ++c) {
+    double ds = 0.0;
+    for (size_t t = 0; t < n2; ++t) {
+      ds += dout[c * n2 + t] * T->y[c * n2 + t];
+      dy[c * n2 + t] = T->s[c] * dout[c * n2 + t];
+    }
+    dz[c] = ds * T->s[c] * (1.0 - T->s[c]);
+  }
+  for (int c = 0; c < co; ++c)
+    for (int j = 0; j < 3; ++j) {
+      int cc = c + j - 1;
+      if (cc < 0 || cc >= co) continue;
+      G->eca[j] += dz[c] * T->g[cc];
+      /* dg[cc] += dz[c] * k[j]; g = mean(y) */
+      double dg = dz[c] * k->eca[j] / (double)n2;
+      for (size_t t = 0; t < n2; ++t) dy[cc * n2 + t] += dg;
+    }
+  free(dz);
+  /* y = ReLU(BN(u)) + res(x) */
+  double* dbn = malloc(sizeof(double) * co * n2);
+  for (int c = 0; c < co; ++c) {
+    double is = 1.0 / sqrt(k->v[c] + BN_EPS);
+    for (size_t t = 0; t < n2; ++t) {
+      double bn = k->g[c] * (T->u[c * n2 + t] - k->m[c]) * is + k->b[c];
+      dbn[c * n2 + t] = bn > 0.0 ? dy[c * n2 + t] : 0.0;
+    }
+  }
+  double* du = calloc(co * n2, sizeof(double));
+  batchnorm_bwd(T->u, co, (int)n2, k->g, k->m, k->v, dbn, du, G->g, G->b);
+  free(dbn);
+  double* dx1 = calloc(ci * n, sizeof(double));
+  if (k->enc) {
+    conv2d_bwd(T->x1, ci, h, w, k->w2, co, 3, 2, 1, 1, du, dx1, G->w2, NULL);
+    conv2d_bwd(T->x, ci, h, w, k->rw, co, 3, 2, 1, 1, dy, dx, G->rw, G->rb);
+  } else {
+    conv_transpose2d_bwd(T->x1, ci, h, w, k->w2, co, 4, 2, 1, 1, du, dx1, G->w2, NULL);
+    conv_transpose2d_bwd(T->x, ci, h, w, k->rw, co, 4, 2, 1, 1, dy, dx, G->rw, G->rb);
+  }
+  free(du);
+  free(dy);
+  /* x1 = ReLU(BN1(t1) + BN2(t2) + BN3(x)) */
+  for (size_t t = 0; t < ci * n; ++t)
+    if (T->x1[t] <= 0.0) dx1[t] = 0.0;
+  double* dt1 = calloc(ci * n, sizeof(double));
+  double* dt2 = calloc(ci * n, sizeof(double));
+  batchnorm_bwd(T->t1, ci, (int)n, k->g1, k->m1, k->v1, dx1, dt1, G->g1, G->b1);
+  batchnorm_bwd(T->t2, ci, (int)n, k->g2, k->m2, k->v2, dx1, dt2, G->g2, G->b2);
+  batchnorm_bwd(T->x, ci, (int)n, k->g3, k->m3, k->v3, dx1, dx, G->g3, G->b3);
+  if (k->enc) {
+    conv2d_bwd(T->x, ci, h, w, k->w1, ci, 1, 1, 0, ci, dt1, dx, G->w1, NULL);
+    conv2d_bwd(T->x, ci, h, w, k->w3, ci, 3, 1, 1, ci, dt2, dx, G->w3, NULL);
+  } else {
+    conv_transpose2d_bwd(T->x, ci, h, w, k->w1, ci, 1, 1, 0, ci, dt1, dx, G->w1, NULL);
+    conv_transpose2d_bwd(T->x, ci, h, w, k->w3, ci, 3, 1, 1, ci, dt2, dx, G->w3, NULL);
+  }
+  free(dt1); free(dt2); free(dx1);
+}
+
+static void tape_free(blk_tape* T) {
+  free(T->x); free(T->t1); free(T->t2); free(T->x1); free(T->u); free(T->y); free(T->g); free(T->s);
+}
+
+/* dL/dtheta and dL/dx of one window given dL/dz (gout [H][W]); the
+ * gradients are accumulated into gparams (canonical order) and gin
+ * ([3][H][W], may be NULL). */
+static int adjoint_one(const orc_net* net, const float* in, const double* gout, int H, int W, double* gp,
+                       double* gin) {
+  if (H <= 0 || W <= 0 || H % 8 || W % 8) return -1;
+  size_t n = (size_t)H * W;
+  /* gradient pointers mirror the parameter layout */
+  double* q = gp;
+  double *gstem_w = q, *gstem_g = q + 216, *gstem_b = q + 224;
+  q += 232;
+  blk_grad G[6];
+  for (int b = 0; b < 6; ++b) {
+    int ci = BLK_CIN[b], co = blk_cout(b);
+    G[b].w1 = q; q += ci;
+    G[b].g1 = q; q += ci;
+    G[b].b1 = q; q += ci;
+    G[b].w3 = q; q += 9 * ci;
+    G[b].g2 = q; q += ci;
+    G[b].b2 = q; q += ci;
+    G[b].g3 = q; q += ci;
+    G[b].b3 = q; q += ci;
+    G[b].w2 = q; q += blk_dense(b);
+    G[b].g = q; q += co;
+    G[b].b = q; q += co;
+    G[b].rw = q; q += blk_dense(b);
+    G[b].rb = q; q += co;
+    G[b].eca = q; q += 3;
+  }
+  double *gout_w = q, *gout_b = q + 72;
+  /* forward with tape */
+  double* x = malloc(sizeof(double) * 3 * n);
+  for (size_t t = 0; t < 3 * n; ++t) x[t] = (double)in[t];
+  double* su = malloc(sizeof(double) * 8 * n); /* stem conv output */
+  orc_conv2d(x, 3, H, W, net->stem_w, NULL, 8, 3, 1, 1, 1, su);
+  double* a = dup(su, 8 * n);
+  batchnorm(a, 8, (int)n, net->stem_g, net->stem_b, net->stem_m, net->stem_v);
+  relu(a, 8 * n);
+  blk_tape T[6];
+  double* outs[6];
+  double* stem_out = a;
+  int h = H, w = W;
+  for (int b = 0; b < 6; ++b) {
+    outs[b] = block_forward_tape(&net->blk[b], a, h, w, &T[b]);
+    size_t sz = (size_t)net->blk[b].cout * T[b].H2 * T[b].W2;
+    if (b == 3 || b == 4) {
+      const double* s = outs[4 - b];
+      for (size_t t = 0; t < sz; ++t) outs[b][t] += s[t];
+    }
+    a = outs[b];
+    h = T[b].H2;
+    w = T[b].W2;
+  }
+  free(stem_out);
+  /* outs[0..5] hold the block outputs (post ECA, post skip); a == outs[5] */
+  double* zl = malloc(sizeof(double) * n);
+  orc_conv2d(a, 8, H, W, net->out_w, net->out_b, 1, 3, 1, 1, 1, zl);
+  /* output: z = sigmoid(zl) */
+  double* dzl = malloc(sizeof(double) * n);
+  for (size_t t = 0; t < n; ++t) {
+    double z = 1.0 / (1.0 + exp(-zl[t]));
+    dzl[t] = gout[t] * z * (1.0 - z);
+  }
+  double* dcur = calloc(8 * n, sizeof(double));
+  conv2d_bwd(a, 8, H, W, net->out_w, 1, 3, 1, 1, 1, dzl, dcur, gout_w, gout_b);
+  free(zl); free(dzl);
+  /* blocks in reverse; skip sources collect extra gradient */
+  double* dskip[2] = {calloc((size_t)16 * (H / 2) * (W / 2), sizeof(double)),
+                      calloc((size_t)32 * (H / 4) * (W / 4), sizeof(double))};
+  for (int b = 5; b >= 0; --b) {
+    size_t osz = (size_t)net->blk[b].cout * T[b].H2 * T[b].W2;
+    if (b == 0 || b == 1)
+      for (size_t t = 0; t < osz; ++t) dcur[t] += dskip[b][t];
+    if (b == 3 || b == 4)
+      for (size_t t = 0; t < osz; ++t) dskip[4 - b][t] += dcur[t];
+    size_t isz = (size_t)net->blk[b].cin * T[b].h * T[b].w;
+    double* dx = calloc(isz, sizeof(double));
+    block_backward(&net->blk[b], &T[b], dcur, dx, &G[b]);
+    free(dcur);
+    dcur = dx;
+  }
+  /* stem: a0 = ReLU(BN(su)) */
+  for (size_t t = 0; t < 8 * n; ++t)
+    if (T[0].x[t] <= 0.0) dcur[t] = 0.0;
+  double* dsu = calloc(8 * n, sizeof(double));
+  batchnorm_bwd(su, 8, (int)n, net->stem_g, net->stem_m, net->stem_v, dcur, dsu, gstem_g, gstem_b);
+  conv2d_bwd(x, 3, H, W, net->stem_w, 8, 3, 1, 1, 1, dsu, gin, gstem_w, NULL);
+  free(dsu); free(dcur); free(su); free(x);
+  for (int b = 0; b < 6; ++b) {
+    tape_free(&T[b]);
+    free(outs[b]);
+  }
+  free(dskip[0]);
+  free(dskip[1]);
+  return 0;
+}
+
+int orc_adjoint(const float* params, const float* buffers, const float* in, const double* gout, int H, int W,
+                double* gparams, double* gin) {
+  orc_net net;
+  net_load(&net, params, buffers);
+  memset(gparams, 0, sizeof(double) * orc_num_params());
+  if (gin) memset(gin, 0, sizeof(double) * 3 * H * W);
+  int rc = adjoint_one(&net, in, gout, H, W, gparams, gin);
+  net_free(&net);
+  return rc;
+}
+
+typedef struct {
+  const orc_net* net;
+  const float *in, *target;
+  int B, H, W, tid, nt, rc;
+  double loss;
+  double* gp;
+} grad_job;
+
+static void* grad_worker(void* arg) {
+  grad_job* j = (grad_job*)arg;
+  size_t n = (size_t)j->H * j->W;
+  double* z = malloc(sizeof(double) * n);
+  double* gz = malloc(sizeof(double) * n);
+  double N = (double)j->B * (double)n;
+  for (int b = j->tid; b < j->B; b += j->nt) {
+    int rc = forward_one(j->net, j->in + (size_t)b * 3 * n, j->H, j->W, z, NULL);
+    if (rc) { j->rc = rc; continue; }
+    for (size_t t = 0; t < n; ++t) {
+      double e = z[t] - (double)j->target[(size_t)b * n + t];
+      j->loss += e * e / N;
+      gz[t] = 2.0 * e / N;
+    }
+    rc = adjoint_one(j->net, j->in + (size_t)b * 3 * n, gz, j->H, j->W, j->gp, NULL);
+    if (rc) j->rc = rc;
+  }
+  free(z);
+  free(gz);
+  return NULL;
+}
+
+/* Mean squared error over B windows against the clean maps, and its
+ * gradient with respect to every parameter (canonical order). Threads
+ * accumulate into private buffers that are summed in a fixed order. */
+double orc_loss_grad(const float* params, const float* buffers, const float* in, const float* target, int B,
+                     int H, int W, double* gparams, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > B) nthreads = B;
+  if (nthreads > 256) nthreads = 256;
+  orc_net net;
+  net_load(&net, params, buffers);
+  int np = orc_num_params();
+  pthread_t th[256];
+  grad_job jobs[256];
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t] = (grad_job){&net, in, target, B, H, W, t, nthreads, 0, 0.0, calloc(np, sizeof(double))};
+    pthread_create(&th[t], NULL, grad_worker, &jobs[t]);
+  }
+  double loss = 0.0;
+  memset(gparams, 0, sizeof(double) * np);
+  int rc = 0;
+  for (int t = 0; t < nthreads; ++t) {
+    pthread_join(th[t], NULL);
+    loss += jobs[t].loss;
+    for (int i = 0; i < np; ++i) gparams[i] += jobs[t].gp[i];
+    free(jobs[t].gp);
+    if (jobs[t].rc) rc = jobs[t].rc;
+  }
+  net_free(&net);
+  return rc ? NAN : loss;
+}
+
+/* ======================================================================== */
 /* Metrics (Sec. V-B).                                                      */
 /* ======================================================================== */
 

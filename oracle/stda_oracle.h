@@ -111,6 +111,19 @@ void orc_conv_transpose2d(const double* x, int Ci, int H, int W,
                           int stride, int pad, int groups, double* y);
 void orc_eca(double* m, int C, int h, int w, const double* k3);
 
+/* Adjoint of the forward pass for one window: given dL/dz (gout [H][W]),
+ * writes dL/dtheta (gparams[num_params], canonical order) and, if gin is not
+ * NULL, dL/dx (gin [3][H][W]). */
+int orc_adjoint(const float* params, const float* buffers, const float* in,
+                const double* gout, int H, int W, double* gparams,
+                double* gin);
+
+/* Mean squared error over B windows against target maps [B][H][W] and its
+ * gradient with respect to every parameter. Returns the loss. */
+double orc_loss_grad(const float* params, const float* buffers,
+                     const float* in, const float* target, int B, int H,
+                     int W, double* gparams, int nthreads);
+
 /* ---- metrics (Sec. V-B) ---- */
 double orc_sinr_db(const double* z, int P, int Q, const int* bins, int nb,
                    int guard);

@@ -17,3 +17,7 @@ def weights():
     from paper_2307_09063_gb300 import inputs
 
     return inputs.init_params(0)
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)
