@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--workload", default="bf16_b256_3x256x128",
                     help="bf16_b256_3x256x128 | fp8_b1024_3x512x256 | fp32_b1_3x64x64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the fwd+bwd training-step measurement")
+    ap.add_argument("--train-steps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -280,6 +282,38 @@ def main():
         e2e_ms = float(t.item())
     e2e_value = world * B * args.steps / (e2e_ms / 1e3)
 
+    # fwd + bwd: the training step (stda_backward, MSE against the clean maps)
+    # on 64 windows of 3 x 256 x 128, one step per timed iteration
+    train = None
+    if not args.no_train and world >= 1:
+        wt = workload("train_bf16_b64_3x256x128")
+        gt = wt.gen
+        tctx = stda.Context(gt.P, gt.Q, wt.batch, "bf16", 0)
+        tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, rank * wt.batch, wt.batch, dtype=torch.bfloat16)
+        for _ in range(2):
+            tctx.backward(tx, target=tclean)
+        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.train_steps)]
+        barrier()
+        for i in range(args.train_steps):
+            flush.fill_(i & 0xFF)
+            tev[i][0].record(stream)
+            tctx.backward(tx, target=tclean)
+            tev[i][1].record(stream)
+        barrier()
+        tms = [a.elapsed_time(b) for a, b in tev]
+        ttot = sum(tms)
+        if dist:
+            t = torch.tensor([ttot], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ttot = float(t.item())
+        train = {"value": world * wt.batch * args.train_steps / (ttot / 1e3), "unit": UNIT,
+                 "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
+                 "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
+                 "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
+                 "l2": "flushed between timed steps"}
+        del tctx
+
     hbm_gbs, bf16_tf, bf16_tf_sus, peak_src = load_peaks()
     bytes_per_step = B * 4 * H * W * esz  # 3 input maps + 1 output map per window
     hbm_achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
@@ -322,6 +356,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * esz),
                     "d2h_bytes_per_step": int(oh.numel() * esz)},
             "clocks": clk.summary(), "gpu_launches": int(launches)}
+    if train:
+        line["train_fwd_bwd"] = train
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

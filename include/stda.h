@@ -122,6 +122,28 @@ stda_status stda_set_buffers(stda_ctx* ctx, const float* host_src, size_t n);
 stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
                          int H, int W, struct CUstream_st* stream);
 
+/* Training step (adjoint of the forward pass): runs the network's forward
+ * pass with a tape and its exact adjoint, in FP32 on the CUDA cores, with
+ * batch normalisation in inference form (frozen running statistics;
+ * gamma and beta receive gradients). Weight and BN gradients are reduced
+ * per chunk of four windows in FP32 and across chunks in FP64; the loss is
+ * an FP64 sum.
+ *   d_in      [B][3][H][W] in the context's element type
+ *   d_target  [B][1][H][W] clean maps in the context's element type; the
+ *             loss is their mean squared error (Sec. V-C trains the
+ *             denoiser against interference-free maps), or NULL
+ *   d_gout    [B][1][H][W] float dL/dz, used when d_target is NULL
+ *   d_gparams [137915] float dL/dtheta in canonical order (required)
+ *   d_loss    double, the loss (target mode), or NULL
+ *   d_gin     [B][3][H][W] float dL/dx, or NULL
+ *   d_out     [B][1][H][W] float forward output of the training graph, or NULL
+ * The first call allocates the context's training workspace (for
+ * max_batch windows of the context's H x W). */
+stda_status stda_backward(stda_ctx* ctx, const void* d_in, const void* d_target,
+                          const float* d_gout, float* d_gparams, double* d_loss,
+                          float* d_gin, float* d_out, int B, int H, int W,
+                          struct CUstream_st* stream);
+
 /* Sticky device-side error word of the context (STDA_OK or
  * STDA_ERR_TIMEOUT); synchronises the context's last stream. */
 stda_status stda_device_status(stda_ctx* ctx);

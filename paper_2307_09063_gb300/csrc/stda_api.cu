@@ -9,6 +9,7 @@
 
 #include "stda_internal.h"
 #include "stda_tc.h"
+#include "stda_train.h"
 
 namespace stda {
 
@@ -333,6 +334,10 @@ struct stda_ctx {
   stda::TcPackOffsets tc_off;
   stda::TcWeights tcw;
   bool force_simt = false;  // STDA_FORCE_SIMT=1: BF16 on the CUDA-core kernels
+  float* d_canon = nullptr;  // canonical parameters + BN buffers (training graph)
+  void* d_train = nullptr;   // training workspace
+  size_t train_bytes = 0;
+  float* d_target32 = nullptr;  // float copy of bf16 targets
   void* d_scratch = nullptr;
   size_t scratch_size = 0;
   int* d_status = nullptr;
@@ -378,6 +383,13 @@ stda_status upload_weights(stda_ctx* c) {
   if ((e = cudaMemcpy(c->d_tc, blob.data(), blob.size(), cudaMemcpyHostToDevice)))
     return cuda_fail(c, e, "upload tc weights");
   c->tcw = stda::tc_weights_from(c->d_tc, c->tc_off);
+  if (!c->d_canon &&
+      (e = cudaMalloc((void**)&c->d_canon, sizeof(float) * (stda::kNumParams + stda::kNumBuffers))))
+    return cuda_fail(c, e, "alloc canonical parameters");
+  if ((e = cudaMemcpy(c->d_canon, c->params.data(), sizeof(float) * stda::kNumParams, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->d_canon + stda::kNumParams, c->buffers.data(), sizeof(float) * stda::kNumBuffers,
+                      cudaMemcpyHostToDevice)))
+    return cuda_fail(c, e, "upload canonical parameters");
   return STDA_OK;
 }
 
@@ -452,6 +464,9 @@ stda_status stda_destroy(stda_ctx* c) {
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_tc) cudaFree(c->d_tc);
+  if (c->d_canon) cudaFree(c->d_canon);
+  if (c->d_train) cudaFree(c->d_train);
+  if (c->d_target32) cudaFree(c->d_target32);
   delete c;
   return STDA_OK;
 }
@@ -524,6 +539,61 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
       return fail(c, STDA_ERR_UNSUPPORTED, "forward: unknown precision");
   }
   if (e) return cuda_fail(c, e, "forward");
+  return STDA_OK;
+}
+
+namespace {
+__global__ void k_bf16_to_f32_flat(const __nv_bfloat16* a, float* o, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = __bfloat162float(a[i]);
+}
+}  // namespace
+
+stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, const float* d_gout,
+                          float* d_gparams, double* d_loss, float* d_gin, float* d_out, int B, int H, int W,
+                          cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (B < 0 || B > c->cfg.max_batch) return fail(c, STDA_ERR_SHAPE, "backward: batch out of range");
+  if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "backward: H and W must be positive multiples of 8");
+  if ((size_t)B * H * W > (size_t)c->cfg.max_batch * c->cfg.H * c->cfg.W)
+    return fail(c, STDA_ERR_SHAPE, "backward: B*H*W exceeds the context");
+  if (!d_in || !d_gparams || (!d_target && !d_gout))
+    return fail(c, STDA_ERR_INVALID_ARG, "backward: null pointer");
+  cudaError_t e;
+  if (!c->d_train) {
+    size_t need = stda::train_workspace_bytes(c->cfg.max_batch, c->cfg.H, c->cfg.W) +
+                  (size_t)c->cfg.max_batch * 3 * c->cfg.H * c->cfg.W * sizeof(float) + 256;
+    if ((e = cudaMalloc(&c->d_train, need))) return cuda_fail(c, e, "backward: workspace");
+    c->train_bytes = need;
+  }
+  const bool bf = c->cfg.prec != STDA_FP32;
+  const float* target = (const float*)d_target;
+  if (d_target && bf) {
+    if (!c->d_target32 &&
+        (e = cudaMalloc((void**)&c->d_target32, sizeof(float) * c->cfg.max_batch * c->cfg.H * c->cfg.W)))
+      return cuda_fail(c, e, "backward: target buffer");
+    long n = (long)B * H * W;
+    k_bf16_to_f32_flat<<<(int)((n + 255) / 256), 256, 0, st>>>((const __nv_bfloat16*)d_target, c->d_target32, n);
+    target = c->d_target32;
+  }
+  stda::TrainArgs a{};
+  a.params = c->d_canon;
+  a.buffers = c->d_canon + stda::kNumParams;
+  a.in = d_in;
+  a.in_bf16 = bf;
+  a.target = target;
+  a.gout = d_target ? nullptr : d_gout;
+  a.gparams = d_gparams;
+  a.loss = d_target ? d_loss : nullptr;
+  a.gin = d_gin;
+  a.z_out = d_out;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.stream = st;
+  c->last_stream = st;
+  if (B == 0) return STDA_OK;
+  if ((e = stda::train_step(a, c->d_train, c->train_bytes))) return cuda_fail(c, e, "backward");
   return STDA_OK;
 }
 

@@ -1,0 +1,743 @@
+// Training step of Radar-STDA on the GPU: forward with a tape, mean squared
+// error against the clean maps (or a given dL/dz), and the adjoint of every
+// operation, producing dL/dtheta for all 137,915 parameters.
+//
+// The graph keeps batch normalisation unfolded (inference form with frozen
+// running statistics; gamma and beta are trained), so every tensor of the
+// taped forward is the one the adjoint needs. Tensors are NCHW float32.
+// Weight and BN gradients are first reduced per batch chunk in FP32 (one
+// thread block per (output, input) channel pair, warp shuffles), then the
+// chunks are summed in FP64 in a fixed order; the loss is an FP64 sum.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "stda_internal.h"
+#include "stda_train.h"
+
+namespace stda {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kChunkWin = 4;  // windows per weight-gradient partial
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+inline dim3 grid1(long n) { return dim3(cdiv(n, kT)); }
+
+// ----------------------------------------------------------- forward ops
+// y[b][o][Y][X] = bias[o] + sum_{i in group(o), ky, kx} x[b][i][Y s - p + ky][X s - p + kx] w[o][i'][ky][kx]
+__global__ void k_conv(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
+                       float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
+                       int Ho, int Wo) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)B * Co * Ho * Wo) return;
+  int X = idx % Wo, Y = (idx / Wo) % Ho, o = (idx / ((long)Wo * Ho)) % Co, b = idx / ((long)Wo * Ho * Co);
+  int cig = Ci / g, gi = o / (Co / g);
+  float acc = bias ? bias[o] : 0.f;
+  for (int il = 0; il < cig; ++il) {
+    const float* xp = x + ((size_t)b * Ci + gi * cig + il) * H * W;
+    const float* wp = w + ((size_t)o * cig + il) * k * k;
+    for (int ky = 0; ky < k; ++ky) {
+      int yy = Y * s - p + ky;
+      if (yy < 0 || yy >= H) continue;
+      for (int kx = 0; kx < k; ++kx) {
+        int xx = X * s - p + kx;
+        if (xx < 0 || xx >= W) continue;
+        acc += xp[yy * W + xx] * wp[ky * k + kx];
+      }
+    }
+  }
+  y[idx] = acc;
+}
+
+// transposed: y[b][o][Y][X] = bias[o] + sum x[b][i][yi][xi] w[i][o'][ky][kx], Y = yi s - p + ky
+__global__ void k_convT(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
+                        float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
+                        int Ho, int Wo) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)B * Co * Ho * Wo) return;
+  int X = idx % Wo, Y = (idx / Wo) % Ho, o = (idx / ((long)Wo * Ho)) % Co, b = idx / ((long)Wo * Ho * Co);
+  int cig = Ci / g, cog = Co / g, gi = o / cog, ol = o % cog;
+  float acc = bias ? bias[o] : 0.f;
+  for (int il = 0; il < cig; ++il) {
+    int i = gi * cig + il;
+    const float* xp = x + ((size_t)b * Ci + i) * H * W;
+    const float* wp = w + ((size_t)i * cog + ol) * k * k;
+    for (int ky = 0; ky < k; ++ky) {
+      int ny = Y + p - ky;
+      if (ny < 0 || ny % s) continue;
+      int yi = ny / s;
+      if (yi >= H) continue;
+      for (int kx = 0; kx < k; ++kx) {
+        int nx = X + p - kx;
+        if (nx < 0 || nx % s) continue;
+        int xi = nx / s;
+        if (xi >= W) continue;
+        acc += xp[yi * W + xi] * wp[ky * k + kx];
+      }
+    }
+  }
+  y[idx] = acc;
+}
+
+// dx[b][i][yy][xx] += sum over (o, ky, kx) with yy = Y s - p + ky of dy w (adjoint of k_conv)
+__global__ void k_conv_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
+                             int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)B * Ci * H * W) return;
+  int xx = idx % W, yy = (idx / W) % H, i = (idx / ((long)W * H)) % Ci, b = idx / ((long)W * H * Ci);
+  int cig = Ci / g, cog = Co / g, gi = i / cig, il = i % cig;
+  float acc = 0.f;
+  for (int ol = 0; ol < cog; ++ol) {
+    int o = gi * cog + ol;
+    const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
+    const float* wp = w + ((size_t)o * cig + il) * k * k;
+    for (int ky = 0; ky < k; ++ky) {
+      int ny = yy + p - ky;
+      if (ny < 0 || ny % s) continue;
+      int Y = ny / s;
+      if (Y >= Ho) continue;
+      for (int kx = 0; kx < k; ++kx) {
+        int nx = xx + p - kx;
+        if (nx < 0 || nx % s) continue;
+        int X = nx / s;
+        if (X >= Wo) continue;
+        acc += dp[Y * Wo + X] * wp[ky * k + kx];
+      }
+    }
+  }
+  dx[idx] += acc;
+}
+
+// dx[b][i][yi][xi] += sum_{o', ky, kx} dy[b][o][yi s - p + ky][xi s - p + kx] w[i][o'][ky][kx]
+__global__ void k_convT_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
+                              int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)B * Ci * H * W) return;
+  int xi = idx % W, yi = (idx / W) % H, i = (idx / ((long)W * H)) % Ci, b = idx / ((long)W * H * Ci);
+  int cig = Ci / g, cog = Co / g, gi = i / cig;
+  float acc = 0.f;
+  for (int ol = 0; ol < cog; ++ol) {
+    int o = gi * cog + ol;
+    const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
+    const float* wp = w + ((size_t)i * cog + ol) * k * k;
+    for (int ky = 0; ky < k; ++ky) {
+      int Y = yi * s - p + ky;
+      if (Y < 0 || Y >= Ho) continue;
+      for (int kx = 0; kx < k; ++kx) {
+        int X = xi * s - p + kx;
+        if (X < 0 || X >= Wo) continue;
+        acc += dp[Y * Wo + X] * wp[ky * k + kx];
+      }
+    }
+  }
+  dx[idx] += acc;
+}
+
+__device__ float block_sum(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+  return r;  // valid in thread 0
+}
+
+// Weight gradient of one (output, input) channel pair of a conv (or of a
+// transposed conv when T) over the windows of one chunk: one block per pair,
+// k*k sums per thread, block reduction; part[chunk][pair * k * k + tap].
+template <bool TR>
+__global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ part,
+                        int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo,
+                        int npairs) {
+  __shared__ float sh[32];
+  const int pair = blockIdx.x, chunk = blockIdx.y;
+  const int cig = Ci / g, cog = Co / g;
+  int i, o;
+  if (!TR) {  // pair = o * cig + il
+    o = pair / cig;
+    i = (o / cog) * cig + pair % cig;
+  } else {    // pair = i * cog + ol
+    i = pair / cog;
+    o = (i / cig) * cog + pair % cog;
+  }
+  float acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.f;
+  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
+  if (!TR) {
+    const int n = Ho * Wo;
+    for (int b = b0; b < b1; ++b) {
+      const float* xp = x + ((size_t)b * Ci + i) * H * W;
+      const float* dp = dy + ((size_t)b * Co + o) * n;
+      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        int Y = q / Wo, X = q % Wo;
+        float d = dp[q];
+        for (int ky = 0; ky < k; ++ky) {
+          int yy = Y * s - p + ky;
+          if (yy < 0 || yy >= H) continue;
+          for (int kx = 0; kx < k; ++kx) {
+            int xx = X * s - p + kx;
+            if (xx < 0 || xx >= W) continue;
+            acc[ky * k + kx] += d * xp[yy * W + xx];
+          }
+        }
+      }
+    }
+  } else {
+    const int n = H * W;
+    for (int b = b0; b < b1; ++b) {
+      const float* xp = x + ((size_t)b * Ci + i) * n;
+      const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
+      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        int yi = q / W, xi = q % W;
+        float v = xp[q];
+        for (int ky = 0; ky < k; ++ky) {
+          int Y = yi * s - p + ky;
+          if (Y < 0 || Y >= Ho) continue;
+          for (int kx = 0; kx < k; ++kx) {
+            int X = xi * s - p + kx;
+            if (X < 0 || X >= Wo) continue;
+            acc[ky * k + kx] += v * dp[Y * Wo + X];
+          }
+        }
+      }
+    }
+  }
+  for (int t = 0; t < k * k; ++t) {
+    float r = block_sum(acc[t], sh);
+    if (threadIdx.x == 0) part[(size_t)chunk * npairs * k * k + (size_t)pair * k * k + t] = r;
+  }
+}
+
+// Per-channel sums over one chunk of windows: S1 = sum a, S2 = sum a (v - mean) / sqrt(var + eps)
+// (S2 only if v); part[chunk][c][2].
+__global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict__ v, const float* __restrict__ mean,
+                            const float* __restrict__ var, float* __restrict__ part, int B, int C, int n) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x, chunk = blockIdx.y;
+  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
+  float s1 = 0.f, s2 = 0.f;
+  float m = v ? mean[c] : 0.f, is = v ? rsqrtf(var[c] + 1e-5f) : 0.f;
+  for (int b = b0; b < b1; ++b) {
+    const float* ap = a + ((size_t)b * C + c) * n;
+    const float* vp = v ? v + ((size_t)b * C + c) * n : nullptr;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      float d = ap[q];
+      s1 += d;
+      if (vp) s2 += d * (vp[q] - m) * is;
+    }
+  }
+  float r1 = block_sum(s1, sh);
+  float r2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    part[((size_t)chunk * C + c) * 2] = r1;
+    part[((size_t)chunk * C + c) * 2 + 1] = r2;
+  }
+}
+
+// Sums partials over chunks in FP64 (fixed order) and adds them into the
+// gradient accumulator: acc[dst + j] += sum_chunk part[chunk][j * stride + off].
+__global__ void k_reduce(const float* __restrict__ part, int nchunks, int n, int stride, int off,
+                         double* __restrict__ acc, long dst) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += (double)part[(size_t)c * n * stride + (size_t)j * stride + off];
+  acc[dst + j] += s;
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, int n) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = (float)a[j];
+}
+
+// y = relu?(gam (x - mean) / sqrt(var + eps) + bet) per channel
+__global__ void k_bn(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ gam,
+                     const float* __restrict__ bet, const float* __restrict__ mean, const float* __restrict__ var,
+                     long total, int C, int n, int relu) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  float v = gam[c] * (x[idx] - mean[c]) * rsqrtf(var[c] + 1e-5f) + bet[c];
+  y[idx] = relu ? fmaxf(v, 0.f) : v;
+}
+
+// stage 1: x1 = ReLU(BN1(t1) + BN2(t2) + BN3(x))
+struct BnP {
+  const float *g, *b, *m, *v;
+};
+__device__ __forceinline__ float bnv(const BnP& q, int c, float x) {
+  return q.g[c] * (x - q.m[c]) * rsqrtf(q.v[c] + 1e-5f) + q.b[c];
+}
+__global__ void k_stage1(const float* t1, const float* t2, const float* x, float* x1, BnP b1, BnP b2, BnP b3,
+                         long total, int C, int n) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  x1[idx] = fmaxf(bnv(b1, c, t1[idx]) + bnv(b2, c, t2[idx]) + bnv(b3, c, x[idx]), 0.f);
+}
+// y = ReLU(BN(u)) + r
+__global__ void k_stage2(const float* u, const float* r, float* y, BnP bn, long total, int C, int n) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  y[idx] = fmaxf(bnv(bn, c, u[idx]), 0.f) + r[idx];
+}
+
+// per (b, c): g = mean over the map
+__global__ void k_gap(const float* __restrict__ y, float* __restrict__ g, int n) {
+  __shared__ float sh[32];
+  const float* p = y + (size_t)blockIdx.x * n;
+  float s = 0.f;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += p[q];
+  float r = block_sum(s, sh);
+  if (threadIdx.x == 0) g[blockIdx.x] = r / (float)n;
+}
+// per (b, c): s = sigmoid(conv1d_k3(g))
+__global__ void k_eca_s(const float* g, const float* k3, float* sc, int B, int C) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= B * C) return;
+  int c = idx % C;
+  const float* gb = g + (idx - c);
+  float z = k3[1] * gb[c];
+  if (c > 0) z += k3[0] * gb[c - 1];
+  if (c + 1 < C) z += k3[2] * gb[c + 1];
+  sc[idx] = 1.f / (1.f + expf(-z));
+}
+// out = s * y (+ skip)
+__global__ void k_scale(const float* y, const float* sc, const float* skip, float* out, long total, int n) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  float v = sc[idx / n] * y[idx];
+  out[idx] = skip ? v + skip[idx] : v;
+}
+
+// output: z = sigmoid(logit); MSE gradient (or given gout) -> dlogit;
+// per-block FP64 loss partials
+__global__ void k_out_loss(const float* logit, const float* target, const float* gout, float* z, float* dlogit,
+                           double* loss_part, long total, double inv_n) {
+  __shared__ double sh[32];
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e2 = 0.0;
+  if (idx < total) {
+    float zz = 1.f / (1.f + expf(-logit[idx]));
+    z[idx] = zz;
+    float g;
+    if (target) {
+      double e = (double)zz - (double)target[idx];
+      e2 = e * e * inv_n;
+      g = (float)(2.0 * e * inv_n);
+    } else {
+      g = gout[idx];
+    }
+    dlogit[idx] = g * zz * (1.f - zz);
+  }
+  for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    loss_part[blockIdx.x] = s;
+  }
+}
+__global__ void k_sum_f64(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+// ---------------------------------------------------------- backward ops
+// per (b, c): ds = sum dout * y
+__global__ void k_eca_ds(const float* dout, const float* y, float* ds, int n) {
+  __shared__ float sh[32];
+  const float* a = dout + (size_t)blockIdx.x * n;
+  const float* v = y + (size_t)blockIdx.x * n;
+  float s = 0.f;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += a[q] * v[q];
+  float r = block_sum(s, sh);
+  if (threadIdx.x == 0) ds[blockIdx.x] = r;
+}
+// per window b (one thread per b): dz = ds s (1 - s); dk partial; dg
+__global__ void k_eca_back(const float* ds, const float* sc, const float* g, const float* k3, float* dgm,
+                           float* dk_part, int B, int C, int n) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float *dsb = ds + b * C, *sb = sc + b * C, *gb = g + b * C;
+  float* dg = dgm + b * C;
+  float dk[3] = {0.f, 0.f, 0.f};
+  for (int c = 0; c < C; ++c) dg[c] = 0.f;
+  for (int c = 0; c < C; ++c) {
+    float dz = dsb[c] * sb[c] * (1.f - sb[c]);
+    for (int j = 0; j < 3; ++j) {
+      int cc = c + j - 1;
+      if (cc < 0 || cc >= C) continue;
+      dk[j] += dz * gb[cc];
+      dg[cc] += dz * k3[j] / (float)n;
+    }
+  }
+  for (int j = 0; j < 3; ++j) dk_part[b * 3 + j] = dk[j];
+}
+// dy = s * dout + dg (the mean's adjoint, already divided by n)
+__global__ void k_eca_dy(const float* dout, const float* sc, const float* dgm, float* dy, long total, int n) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  dy[idx] = sc[idx / n] * dout[idx] + dgm[idx / n];
+}
+// dbn = dy [BN(u) > 0]
+__global__ void k_relu_bn_mask(const float* dy, const float* u, BnP bn, float* dbn, long total, int C, int n) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  dbn[idx] = bnv(bn, c, u[idx]) > 0.f ? dy[idx] : 0.f;
+}
+// out (+)= a * gam / sqrt(var + eps)
+__global__ void k_bn_dx(const float* a, BnP bn, float* out, long total, int C, int n, int accumulate) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  float v = a[idx] * bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
+  out[idx] = accumulate ? out[idx] + v : v;
+}
+// dv = dx1 [x1 > 0]
+__global__ void k_relu_mask(const float* d, const float* act, float* out, long total) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  out[idx] = act[idx] > 0.f ? d[idx] : 0.f;
+}
+__global__ void k_add(float* a, const float* b, long total) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < total) a[idx] += b[idx];
+}
+__global__ void k_bf16_to_f32(const __nv_bfloat16* a, float* out, long total) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < total) out[idx] = __bfloat162float(a[idx]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host
+// Canonical parameter and buffer offsets (same order as the parameter blob).
+struct Canon {
+  int stem_w, stem_g, stem_b, stem_m, stem_v;
+  int w1[6], g1[6], b1[6], w3[6], g2[6], b2[6], g3[6], b3[6], w2[6], g[6], be[6], rw[6], rb[6], eca[6];
+  int m1[6], v1[6], m2[6], v2[6], m3[6], v3[6], m[6], v[6];
+  int out_w, out_b;
+};
+
+static Canon canon() {
+  Canon o;
+  int p = 0, q = 0;
+  o.stem_w = p; p += 216;
+  o.stem_g = p; p += 8;
+  o.stem_b = p; p += 8;
+  o.stem_m = q; q += 8;
+  o.stem_v = q; q += 8;
+  for (int b = 0; b < kNumBlocks; ++b) {
+    int ci = kBlkCin[b], co = kBlkCout[b], dense = (kBlkEnc[b] ? 9 : 16) * ci * co;
+    o.w1[b] = p; p += ci;
+    o.g1[b] = p; p += ci;
+    o.b1[b] = p; p += ci;
+    o.w3[b] = p; p += 9 * ci;
+    o.g2[b] = p; p += ci;
+    o.b2[b] = p; p += ci;
+    o.g3[b] = p; p += ci;
+    o.b3[b] = p; p += ci;
+    o.w2[b] = p; p += dense;
+    o.g[b] = p; p += co;
+    o.be[b] = p; p += co;
+    o.rw[b] = p; p += dense;
+    o.rb[b] = p; p += co;
+    o.eca[b] = p; p += 3;
+    o.m1[b] = q; q += ci;
+    o.v1[b] = q; q += ci;
+    o.m2[b] = q; q += ci;
+    o.v2[b] = q; q += ci;
+    o.m3[b] = q; q += ci;
+    o.v3[b] = q; q += ci;
+    o.m[b] = q; q += co;
+    o.v[b] = q; q += co;
+  }
+  o.out_w = p; p += 72;
+  o.out_b = p;
+  return o;
+}
+
+namespace {
+// Bump allocator over one device buffer.
+struct Arena {
+  char* base;
+  size_t off, cap;
+  float* f(size_t n) { return (float*)take(n * sizeof(float)); }
+  double* d(size_t n) { return (double*)take(n * sizeof(double)); }
+  void* take(size_t bytes) {
+    size_t o = (off + 255) / 256 * 256;
+    off = o + bytes;
+    return base ? base + o : nullptr;
+  }
+};
+
+struct BlkTape {
+  int h, w, H2, W2;
+  float *x, *t1, *t2, *x1, *u, *r, *y, *g, *s, *out;
+};
+}  // namespace
+
+size_t train_workspace_bytes(int B, int H, int W) {
+  TrainArgs a{};
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  Arena ar{nullptr, 0, 0};
+  return train_step_plan(a, &ar);
+}
+
+// Plans (base == nullptr) or runs the whole training step. Returns the
+// workspace bytes used.
+size_t train_step_plan(const TrainArgs& a, void* arena_v) {
+  Arena& ar = *(Arena*)arena_v;
+  const bool run = ar.base != nullptr;
+  const Canon C = canon();
+  const int B = a.B, H = a.H, W = a.W;
+  const size_t n0 = (size_t)H * W;
+  cudaStream_t st = a.stream;
+  const float* P = a.params;
+  const float* Q = a.buffers;
+  auto bnp = [&](int g, int b, int m, int v) { return BnP{P + g, P + b, Q + m, Q + v}; };
+
+  // ---- forward with tape
+  float* xin = ar.f((size_t)B * 3 * n0);
+  if (run) {
+    if (a.in_bf16)
+      k_bf16_to_f32<<<grid1((long)B * 3 * n0), kT, 0, st>>>((const __nv_bfloat16*)a.in, xin, (long)B * 3 * n0);
+    else
+      cudaMemcpyAsync(xin, a.in, sizeof(float) * B * 3 * n0, cudaMemcpyDeviceToDevice, st);
+  }
+  auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
+                  int k, int s, int p, int g, bool tr, int Ho, int Wo) {
+    if (!run) return;
+    long n = (long)B * Co * Ho * Wo;
+    if (tr)
+      k_convT<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+    else
+      k_conv<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+  };
+  float* su = ar.f((size_t)B * 8 * n0);
+  float* a0 = ar.f((size_t)B * 8 * n0);
+  conv(xin, P + C.stem_w, nullptr, su, 3, H, W, 8, 3, 1, 1, 1, false, H, W);
+  if (run) {
+    long n = (long)B * 8 * n0;
+    k_bn<<<grid1(n), kT, 0, st>>>(su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v, n, 8, (int)n0, 1);
+  }
+  BlkTape T[6];
+  const float* cur = a0;
+  int h = H, w = W;
+  for (int b = 0; b < 6; ++b) {
+    const int ci = kBlkCin[b], co = kBlkCout[b];
+    const bool enc = kBlkEnc[b];
+    BlkTape& t = T[b];
+    t.h = h;
+    t.w = w;
+    t.H2 = enc ? h / 2 : 2 * h;
+    t.W2 = enc ? w / 2 : 2 * w;
+    const size_t n = (size_t)h * w, n2 = (size_t)t.H2 * t.W2;
+    t.x = (float*)cur;
+    t.t1 = ar.f((size_t)B * ci * n);
+    t.t2 = ar.f((size_t)B * ci * n);
+    t.x1 = ar.f((size_t)B * ci * n);
+    t.u = ar.f((size_t)B * co * n2);
+    t.r = ar.f((size_t)B * co * n2);
+    t.y = ar.f((size_t)B * co * n2);
+    t.g = ar.f((size_t)B * co);
+    t.s = ar.f((size_t)B * co);
+    t.out = ar.f((size_t)B * co * n2);
+    conv(t.x, P + C.w1[b], nullptr, t.t1, ci, h, w, ci, 1, 1, 0, ci, !enc, h, w);
+    conv(t.x, P + C.w3[b], nullptr, t.t2, ci, h, w, ci, 3, 1, 1, ci, !enc, h, w);
+    if (run)
+      k_stage1<<<grid1((long)B * ci * n), kT, 0, st>>>(t.t1, t.t2, t.x, t.x1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]),
+                                                     bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
+                                                     bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), (long)B * ci * n, ci,
+                                                     (int)n);
+    if (enc) {
+      conv(t.x1, P + C.w2[b], nullptr, t.u, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
+      conv(t.x, P + C.rw[b], P + C.rb[b], t.r, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
+    } else {
+      conv(t.x1, P + C.w2[b], nullptr, t.u, ci, h, w, co, 4, 2, 1, 1, true, t.H2, t.W2);
+      conv(t.x, P + C.rw[b], P + C.rb[b], t.r, ci, h, w, co, 4, 2, 1, 1, true, t.H2, t.W2);
+    }
+    if (run) {
+      long tot = (long)B * co * n2;
+      k_stage2<<<grid1(tot), kT, 0, st>>>(t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), tot, co, (int)n2);
+      k_gap<<<B * co, kT, 0, st>>>(t.y, t.g, (int)n2);
+      k_eca_s<<<cdiv(B * co, kT), kT, 0, st>>>(t.g, P + C.eca[b], t.s, B, co);
+      const float* skip = b == 3 ? T[1].out : b == 4 ? T[0].out : nullptr;
+      k_scale<<<grid1(tot), kT, 0, st>>>(t.y, t.s, skip, t.out, tot, (int)n2);
+    }
+    cur = t.out;
+    h = t.H2;
+    w = t.W2;
+  }
+  float* logit = ar.f((size_t)B * n0);
+  float* z = ar.f((size_t)B * n0);
+  float* dlogit = ar.f((size_t)B * n0);
+  const int nlb = cdiv((long)B * n0, kT);
+  double* lpart = ar.d(nlb);
+  conv(cur, P + C.out_w, P + C.out_b, logit, 8, H, W, 1, 3, 1, 1, 1, false, H, W);
+  if (run) {
+    k_out_loss<<<nlb, kT, 0, st>>>(logit, a.target, a.gout, z, dlogit, lpart, (long)B * n0, 1.0 / ((double)B * n0));
+    if (a.loss) k_sum_f64<<<1, 32, 0, st>>>(lpart, nlb, a.loss);
+    if (a.z_out) cudaMemcpyAsync(a.z_out, z, sizeof(float) * B * n0, cudaMemcpyDeviceToDevice, st);
+  }
+
+  // ---- backward
+  const int nchunk = cdiv(B, kChunkWin);
+  double* gacc = ar.d(kNumParams);
+  if (run) cudaMemsetAsync(gacc, 0, sizeof(double) * kNumParams, st);
+  // largest partial buffer: pairs * k * k per chunk
+  size_t part_max = 0;
+  for (int b = 0; b < 6; ++b) {
+    size_t dense = (size_t)(kBlkEnc[b] ? 9 : 16) * kBlkCin[b] * kBlkCout[b];
+    part_max = std::max(part_max, dense);
+  }
+  part_max = std::max(part_max, (size_t)216);
+  float* part = ar.f(part_max * nchunk);
+  auto wgrad = [&](const float* x, const float* dy, int Ci, int hh, int ww, int Co, int k, int s, int p, int g,
+                   bool tr, int Ho, int Wo, int dst) {
+    if (!run) return;
+    int npairs = tr ? Ci * (Co / g) : Co * (Ci / g);
+    dim3 grid(npairs, nchunk);
+    if (tr)
+      k_wgrad<true><<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo, npairs);
+    else
+      k_wgrad<false><<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo, npairs);
+    int n = npairs * k * k;
+    k_reduce<<<cdiv(n, kT), kT, 0, st>>>(part, nchunk, n, 1, 0, gacc, dst);
+  };
+  auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
+                   int g, bool tr, int Ho, int Wo) {
+    if (!run) return;
+    long n = (long)B * Ci * hh * ww;
+    if (tr)
+      k_convT_dgrad<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+    else
+      k_conv_dgrad<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+  };
+  // per-channel sums of (a) and (a * normalised v) -> dbeta / dgamma (and bias)
+  auto chan = [&](const float* av, const float* v, const float* mean, const float* var, int Cc, int n,
+                  int dgam, int dbet) {
+    if (!run) return;
+    k_chan_sums<<<dim3(Cc, nchunk), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n);
+    if (dbet >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 0, gacc, dbet);
+    if (dgam >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 1, gacc, dgam);
+  };
+  // output conv
+  float* dcur = ar.f((size_t)B * 8 * n0);
+  if (run) cudaMemsetAsync(dcur, 0, sizeof(float) * B * 8 * n0, st);
+  wgrad(cur, dlogit, 8, H, W, 1, 3, 1, 1, 1, false, H, W, C.out_w);
+  chan(dlogit, nullptr, nullptr, nullptr, 1, (int)n0, -1, C.out_b);
+  dgrad(dlogit, P + C.out_w, dcur, 8, H, W, 1, 3, 1, 1, 1, false, H, W);
+  float* dskip0 = ar.f((size_t)B * 16 * (H / 2) * (W / 2));
+  float* dskip1 = ar.f((size_t)B * 32 * (H / 4) * (W / 4));
+  if (run) {
+    cudaMemsetAsync(dskip0, 0, sizeof(float) * B * 16 * (H / 2) * (W / 2), st);
+    cudaMemsetAsync(dskip1, 0, sizeof(float) * B * 32 * (H / 4) * (W / 4), st);
+  }
+  // scratch for one block's adjoint (largest block sizes)
+  size_t big = (size_t)B * 8 * n0;  // every block map holds at most 8 H W values per window
+  float* dy = ar.f(big);
+  float* dtmp = ar.f(big);
+  float* dx1 = ar.f(big);
+  float* dt = ar.f(big);
+  float* ds = ar.f((size_t)B * 64);
+  float* dgm = ar.f((size_t)B * 64);
+  float* dkp = ar.f((size_t)B * 3);
+  float* dxs[2] = {ar.f(big), ar.f(big)};
+  for (int b = 5; b >= 0; --b) {
+    const BlkTape& t = T[b];
+    const int ci = kBlkCin[b], co = kBlkCout[b];
+    const bool enc = kBlkEnc[b];
+    const int n = t.h * t.w, n2 = t.H2 * t.W2;
+    const long tot2 = (long)B * co * n2, tot = (long)B * ci * n;
+    float* dx = dxs[b & 1];
+    if (run) {
+      if (b == 0) k_add<<<grid1(tot2), kT, 0, st>>>(dcur, dskip0, tot2);
+      if (b == 1) k_add<<<grid1(tot2), kT, 0, st>>>(dcur, dskip1, tot2);
+      if (b == 3) k_add<<<grid1(tot2), kT, 0, st>>>(dskip1, dcur, tot2);
+      if (b == 4) k_add<<<grid1(tot2), kT, 0, st>>>(dskip0, dcur, tot2);
+      // ECA
+      k_eca_ds<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
+      k_eca_back<<<cdiv(B, 64), 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
+      k_reduce<<<1, 32, 0, st>>>(dkp, B, 3, 1, 0, gacc, C.eca[b]);
+      k_eca_dy<<<grid1(tot2), kT, 0, st>>>(dcur, t.s, dgm, dy, tot2, n2);
+      // main branch: dbn = dy [BN(u) > 0]; du = dbn gam / sigma
+      BnP bn = bnp(C.g[b], C.be[b], C.m[b], C.v[b]);
+      k_relu_bn_mask<<<grid1(tot2), kT, 0, st>>>(dy, t.u, bn, dtmp, tot2, co, n2);
+    }
+    chan(dtmp, t.u, Q + C.m[b], Q + C.v[b], co, n2, C.g[b], C.be[b]);
+    if (run) {
+      k_bn_dx<<<grid1(tot2), kT, 0, st>>>(dtmp, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), dtmp, tot2, co, n2, 0);
+      cudaMemsetAsync(dx1, 0, sizeof(float) * tot, st);
+      cudaMemsetAsync(dx, 0, sizeof(float) * tot, st);
+    }
+    const int kk = enc ? 3 : 4;
+    wgrad(t.x1, dtmp, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2, C.w2[b]);
+    dgrad(dtmp, P + C.w2[b], dx1, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2);
+    // residual branch
+    wgrad(t.x, dy, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2, C.rw[b]);
+    chan(dy, nullptr, nullptr, nullptr, co, n2, -1, C.rb[b]);
+    dgrad(dy, P + C.rw[b], dx, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2);
+    // stage 1: dv = dx1 [x1 > 0]
+    if (run) k_relu_mask<<<grid1(tot), kT, 0, st>>>(dx1, t.x1, dx1, tot);
+    chan(dx1, t.t1, Q + C.m1[b], Q + C.v1[b], ci, n, C.g1[b], C.b1[b]);
+    chan(dx1, t.t2, Q + C.m2[b], Q + C.v2[b], ci, n, C.g2[b], C.b2[b]);
+    chan(dx1, t.x, Q + C.m3[b], Q + C.v3[b], ci, n, C.g3[b], C.b3[b]);
+    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), dx, tot, ci, n, 1);
+    // dt1 = dv gam1 / sigma1 -> dw1, dx
+    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), dt, tot, ci, n, 0);
+    wgrad(t.x, dt, ci, t.h, t.w, ci, 1, 1, 0, ci, !enc, t.h, t.w, C.w1[b]);
+    dgrad(dt, P + C.w1[b], dx, ci, t.h, t.w, ci, 1, 1, 0, ci, !enc, t.h, t.w);
+    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]), dt, tot, ci, n, 0);
+    wgrad(t.x, dt, ci, t.h, t.w, ci, 3, 1, 1, ci, !enc, t.h, t.w, C.w3[b]);
+    dgrad(dt, P + C.w3[b], dx, ci, t.h, t.w, ci, 3, 1, 1, ci, !enc, t.h, t.w);
+    dcur = dx;
+  }
+  // stem: a0 = ReLU(BN(su))
+  const long tot0 = (long)B * 8 * n0;
+  if (run) k_relu_mask<<<grid1(tot0), kT, 0, st>>>(dcur, a0, dtmp, tot0);
+  chan(dtmp, su, Q + C.stem_m, Q + C.stem_v, 8, (int)n0, C.stem_g, C.stem_b);
+  if (run)
+    k_bn_dx<<<grid1(tot0), kT, 0, st>>>(dtmp, bnp(C.stem_g, C.stem_b, C.stem_m, C.stem_v), dtmp, tot0, 8, (int)n0, 0);
+  wgrad(xin, dtmp, 3, H, W, 8, 3, 1, 1, 1, false, H, W, C.stem_w);
+  if (a.gin) {
+    float* gin = ar.f((size_t)B * 3 * n0);
+    if (run) {
+      cudaMemsetAsync(gin, 0, sizeof(float) * B * 3 * n0, st);
+      dgrad(dtmp, P + C.stem_w, gin, 3, H, W, 8, 3, 1, 1, 1, false, H, W);
+      cudaMemcpyAsync(a.gin, gin, sizeof(float) * B * 3 * n0, cudaMemcpyDeviceToDevice, st);
+    }
+  }
+  if (run) {
+    if (a.gparams_f64) cudaMemcpyAsync(a.gparams_f64, gacc, sizeof(double) * kNumParams, cudaMemcpyDeviceToDevice, st);
+    if (a.gparams) k_to_f32<<<cdiv(kNumParams, kT), kT, 0, st>>>(gacc, a.gparams, kNumParams);
+  }
+  return ar.off;
+}
+
+cudaError_t train_step(const TrainArgs& a, void* workspace, size_t bytes) {
+  Arena ar{(char*)workspace, 0, bytes};
+  size_t need = train_workspace_bytes(a.B, a.H, a.W) + (a.gin ? (size_t)a.B * 3 * a.H * a.W * 4 + 256 : 0);
+  if (need > bytes) return cudaErrorInvalidValue;
+  train_step_plan(a, &ar);
+  return cudaGetLastError();
+}
+
+}  // namespace stda

@@ -64,6 +64,8 @@ def lib():
         L.stda_device_status.argtypes = [_VP]
         L.stda_last_error.restype = ctypes.c_char_p
         L.stda_last_error.argtypes = [_VP]
+        L.stda_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, _VP]
         L.stda_forward_static.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_profile.argtypes = [_VP, ctypes.c_int]
         L.stda_profile_read.restype = ctypes.c_int
@@ -174,6 +176,23 @@ class Context:
         self._check(self.forward_raw(x, out, B, H, W, stream))
         return out
 
+    def backward(self, x, target=None, gout=None, want_gin=False, want_out=False, stream=None):
+        """stda_backward: (loss or None, dL/dtheta [137915] float, dL/dx or None,
+        z or None) for x [B][3][H][W] and either target [B][1][H][W] (MSE) or
+        gout [B][1][H][W] (float dL/dz)."""
+        import torch
+
+        B, _, H, W = x.shape
+        dev = x.device
+        gp = torch.empty(num_params(), dtype=torch.float32, device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev) if target is not None else None
+        gin = torch.empty((B, 3, H, W), dtype=torch.float32, device=dev) if want_gin else None
+        out = torch.empty((B, 1, H, W), dtype=torch.float32, device=dev) if want_out else None
+        st = lib().stda_backward(self.h, _ptr(x), _ptr(target), _ptr(gout), _ptr(gp), _ptr(loss), _ptr(gin),
+                                 _ptr(out), B, H, W, _stream(stream))
+        self._check(st)
+        return loss, gp, gin, out
+
     def profile(self, enable=True):
         self._check(lib().stda_profile(self.h, int(enable)))
 
@@ -230,3 +249,34 @@ def generate(g, seed, cid, w0, B, dtype=None, with_clean=True, device="cuda", st
     if st != OK:
         raise StdaError(st, lib().stda_status_string(st).decode())
     return noisy, clean, bins, ntgt
+
+
+def _autograd_function():
+    import torch
+
+    class STDAFunction(torch.autograd.Function):
+        """z = Radar-STDA(x; theta) through libstda: forward on the context's
+        kernels, backward with stda_backward (the exact adjoint). `params`
+        must hold the context's current parameters (it only routes the
+        gradient to the caller's master copy)."""
+
+        @staticmethod
+        def forward(fctx, x, params, ctx):
+            fctx.save_for_backward(x)
+            fctx.stda = ctx
+            return ctx.forward(x.contiguous())
+
+        @staticmethod
+        def backward(fctx, gout):
+            (x,) = fctx.saved_tensors
+            _, gp, gin, _ = fctx.stda.backward(x.contiguous(), gout=gout.float().contiguous(),
+                                               want_gin=fctx.needs_input_grad[0])
+            gx = gin.to(x.dtype) if gin is not None else None
+            return gx, gp, None
+
+    return STDAFunction
+
+
+def stda_apply(x, params, ctx):
+    """Differentiable application of the denoiser (see STDAFunction)."""
+    return _autograd_function().apply(x, params, ctx)
