@@ -144,6 +144,41 @@ stda_status stda_backward(stda_ctx* ctx, const void* d_in, const void* d_target,
                           float* d_gin, float* d_out, int B, int H, int W,
                           struct CUstream_st* stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous batching of radar streams (the online pattern of Sec. IV-B:
+ * each new frame t is denoised with frames t-1 and t-2 of the same radar).
+ * Frames and outputs are bfloat16 [H][W] device buffers, 16-byte aligned;
+ * serving runs the tensor-core forward of the context's precision (bf16 for
+ * an STDA_FP32 context). Every radar keeps its last three frames in a
+ * device ring owned by the context.
+ *
+ * stda_submit copies d_frame into radar `radar_id`'s ring on `stream` and
+ * returns STDA_WARMUP while the radar has fewer than three frames. From the
+ * third frame on, the window (t, t-1, t-2) joins the pending batch of its
+ * map size; the denoised frame t is written to d_out and `done` (if not
+ * NULL) is recorded once it is there. A new radar is refused with
+ * STDA_ERR_BUSY when its ring (3 H W bf16) plus, for a map size not seen
+ * before, that size's batch buffers would exceed the context's
+ * mem_budget_bytes (0 = no limit); H and W must stay the same for a radar
+ * (else STDA_ERR_SHAPE). A radar whose previous window is still pending
+ * flushes that window's batch first. Batches of 64 windows launch by
+ * themselves. Use one stream for all serving calls of a context. */
+stda_status stda_submit(stda_ctx* ctx, int radar_id, int H, int W,
+                        const void* d_frame, void* d_out,
+                        struct CUevent_st* done, struct CUstream_st* stream);
+/* Launches every pending window: per map size one batch (its own stream,
+ * so sizes overlap), ordered after the frames copied on `stream`. */
+stda_status stda_flush(stda_ctx* ctx, struct CUstream_st* stream);
+/* Releases radar_id's ring (after its pending window has run); blocks until
+ * its size's batches in flight have finished. */
+stda_status stda_serve_close(stda_ctx* ctx, int radar_id,
+                             struct CUstream_st* stream);
+/* Device bytes held by serving (rings and per-size batch buffers), and the
+ * number of open radars. */
+size_t stda_serve_bytes(stda_ctx* ctx);
+int stda_serve_radars(stda_ctx* ctx);
+
 /* Sticky device-side error word of the context (STDA_OK or
  * STDA_ERR_TIMEOUT); synchronises the context's last stream. */
 stda_status stda_device_status(stda_ctx* ctx);

@@ -10,6 +10,7 @@
 #include "stda_internal.h"
 #include "stda_tc.h"
 #include "stda_train.h"
+#include "stda_serve.h"
 
 namespace stda {
 
@@ -338,6 +339,7 @@ struct stda_ctx {
   void* d_train = nullptr;   // training workspace
   size_t train_bytes = 0;
   float* d_target32 = nullptr;  // float copy of bf16 targets
+  stda::Serve* serve = nullptr;
   void* d_scratch = nullptr;
   size_t scratch_size = 0;
   int* d_status = nullptr;
@@ -467,6 +469,7 @@ stda_status stda_destroy(stda_ctx* c) {
   if (c->d_canon) cudaFree(c->d_canon);
   if (c->d_train) cudaFree(c->d_train);
   if (c->d_target32) cudaFree(c->d_target32);
+  if (c->serve) stda::serve_delete(c->serve);
   delete c;
   return STDA_OK;
 }
@@ -596,6 +599,45 @@ stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, c
   if ((e = stda::train_step(a, c->d_train, c->train_bytes))) return cuda_fail(c, e, "backward");
   return STDA_OK;
 }
+
+stda_status stda_submit(stda_ctx* c, int radar, int H, int W, const void* d_frame, void* d_out, cudaEvent_t done,
+                        cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "submit: H and W must be positive multiples of 8");
+  if (!d_frame || !d_out) return fail(c, STDA_ERR_INVALID_ARG, "submit: null pointer");
+  if (((uintptr_t)d_frame | (uintptr_t)d_out) & 15) return fail(c, STDA_ERR_INVALID_ARG, "submit: unaligned buffer");
+  if (!c->serve) c->serve = stda::serve_new(c->d_status);
+  c->last_stream = st;
+  cudaError_t e;
+  stda_status s = stda::serve_submit(c->serve, c->net, c->tcw, c->cfg.mem_budget_bytes, radar, H, W, d_frame, d_out,
+                                     done, st, &e);
+  if (e) return cuda_fail(c, e, "submit");
+  if (s == STDA_ERR_BUSY) return fail(c, s, "submit: memory budget exhausted");
+  if (s == STDA_ERR_SHAPE) return fail(c, s, "submit: radar changed its map size");
+  return s;
+}
+
+stda_status stda_flush(stda_ctx* c, cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (!c->serve) return STDA_OK;
+  c->last_stream = st;
+  cudaError_t e = stda::serve_flush(c->serve, c->net, c->tcw, st);
+  if (e) return cuda_fail(c, e, "flush");
+  return STDA_OK;
+}
+
+stda_status stda_serve_close(stda_ctx* c, int radar, cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (!c->serve) return fail(c, STDA_ERR_INVALID_ARG, "serve_close: unknown radar");
+  cudaError_t e;
+  stda_status s = stda::serve_close(c->serve, c->net, c->tcw, radar, st, &e);
+  if (e) return cuda_fail(c, e, "serve_close");
+  if (s != STDA_OK) return fail(c, s, "serve_close: unknown radar");
+  return s;
+}
+
+size_t stda_serve_bytes(stda_ctx* c) { return c && c->serve ? stda::serve_used(c->serve) : 0; }
+int stda_serve_radars(stda_ctx* c) { return c && c->serve ? stda::serve_radars(c->serve) : 0; }
 
 stda_status stda_device_status(stda_ctx* c) {
   if (!c) return STDA_ERR_INVALID_ARG;

@@ -66,6 +66,13 @@ def lib():
         L.stda_last_error.argtypes = [_VP]
         L.stda_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, _VP]
+        L.stda_submit.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]
+        L.stda_flush.argtypes = [_VP, _VP]
+        L.stda_serve_close.argtypes = [_VP, ctypes.c_int, _VP]
+        L.stda_serve_bytes.restype = ctypes.c_size_t
+        L.stda_serve_bytes.argtypes = [_VP]
+        L.stda_serve_radars.restype = ctypes.c_int
+        L.stda_serve_radars.argtypes = [_VP]
         L.stda_forward_static.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_profile.argtypes = [_VP, ctypes.c_int]
         L.stda_profile_read.restype = ctypes.c_int
@@ -192,6 +199,29 @@ class Context:
                                  _ptr(out), B, H, W, _stream(stream))
         self._check(st)
         return loss, gp, gin, out
+
+    # ----------------------------------------------------------- serving
+    def submit(self, radar, frame, out, done=None, stream=None):
+        """stda_submit: frame / out are bf16 [H][W] CUDA tensors; done an
+        optional torch.cuda.Event. Returns the status (OK, WARMUP or BUSY)."""
+        H, W = frame.shape[-2:]
+        ev = ctypes.c_void_p(done.cuda_event) if done is not None else None
+        st = lib().stda_submit(self.h, radar, H, W, _ptr(frame), _ptr(out), ev, _stream(stream))
+        if st not in (OK, WARMUP, ERR_BUSY):
+            self._check(st)
+        return st
+
+    def flush(self, stream=None):
+        self._check(lib().stda_flush(self.h, _stream(stream)))
+
+    def serve_close(self, radar, stream=None):
+        self._check(lib().stda_serve_close(self.h, radar, _stream(stream)))
+
+    def serve_bytes(self):
+        return int(lib().stda_serve_bytes(self.h))
+
+    def serve_radars(self):
+        return int(lib().stda_serve_radars(self.h))
 
     def profile(self, enable=True):
         self._check(lib().stda_profile(self.h, int(enable)))
