@@ -259,6 +259,35 @@ stda_status stda_generate(const stda_gen_config* g, uint64_t seed,
                           void* d_noisy, void* d_clean, int* d_bins,
                           int* d_ntgt, struct CUstream_st* stream);
 
+/* ------------------------------------------------------------- evaluation */
+
+/* Per-window evaluation of B maps (Sec. V-B), no context needed:
+ *   d_maps   [B][H][W] denoised (or any) maps, bfloat16 if bf16 else float
+ *   d_clean  [B][H][W] interference-free maps (same type), or NULL
+ *   d_bins   [B][16][2] int32 target peak cells (as stda_generate writes)
+ *   d_ntgt   [B] int32 target counts
+ *   d_sinr   [B] double: Eq. (SINR), 10 log10 of the mean z^2 over the
+ *            distinct peak cells over the mean z^2 over the cells outside
+ *            every (2 guard + 1)^2 box around a peak; FP64 sums. Or NULL.
+ *   d_evm    [B] double: Eq. (EVM), mean over the peak cells of
+ *            |clean - z| / |clean| (needs d_clean), or NULL
+ *   d_det    [B][H][W] uint8 CA-CFAR detections, or NULL: cell power z^2
+ *            against alpha times the mean power of the training cells (the
+ *            (2 (cfar_guard + cfar_train) + 1)^2 square minus the
+ *            (2 cfar_guard + 1)^2 guard square, clipped at the edges),
+ *            alpha = N (pfa^(-1/N) - 1) for N training cells
+ *   d_det_rate [B] float: fraction of distinct targets with a detection
+ *            within +-1 cell (the paper's AP without its clustering step),
+ *            or NULL
+ * May allocate temporary device memory (stream-ordered); synchronises the
+ * stream when CA-CFAR runs. */
+stda_status stda_metrics(const void* d_maps, const void* d_clean, int bf16,
+                         const int* d_bins, const int* d_ntgt, int B, int H,
+                         int W, int guard, int cfar_guard, int cfar_train,
+                         double pfa, double* d_sinr, double* d_evm,
+                         float* d_det_rate, unsigned char* d_det,
+                         struct CUstream_st* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,11 @@ def lib():
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
             L.orc_conv_transpose2d.argtypes = L.orc_conv2d.argtypes
             L.orc_eca.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+            L.orc_cacfar.restype = ctypes.c_int
+            L.orc_cacfar.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_ubyte)]
+            L.orc_detect_rate.restype = ctypes.c_double
+            L.orc_detect_rate.argtypes = [ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int, ctypes.c_int, _I, ctypes.c_int]
             L.orc_sinr_db.restype = ctypes.c_double
             L.orc_sinr_db.argtypes = [_D, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int]
             L.orc_evm.restype = ctypes.c_double
@@ -293,3 +298,19 @@ def evm(clean, est, bins):
     c, e = _f64(clean), _f64(est)
     b = np.ascontiguousarray(bins, dtype=np.int32)
     return lib().orc_evm(_p(c, _D), _p(e, _D), c.shape[0], c.shape[1], _p(b, _I), len(b))
+
+
+def cacfar(z, guard=2, train=4, pfa=1e-3):
+    """(detections [P][Q] uint8, count) of CA-CFAR on map z."""
+    z = _f64(z)
+    det = np.zeros(z.shape, dtype=np.uint8)
+    n = lib().orc_cacfar(_p(z, _D), z.shape[0], z.shape[1], guard, train, pfa,
+                         det.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return det, n
+
+
+def detect_rate(det, bins):
+    det = np.ascontiguousarray(det, dtype=np.uint8)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    return lib().orc_detect_rate(det.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), det.shape[0], det.shape[1],
+                                 _p(b, _I), len(b))

@@ -1114,3 +1114,54 @@ double orc_evm(const double* clean, const double* est, int P, int Q,
   free(seen);
   return cnt ? s / cnt : NAN;
 }
+
+/* Cell-averaging CFAR (Sec. V-B: CA-CFAR as the peak detector on RD maps).
+ * Reading: the cell power is z^2 (as in Eq. (SINR)); the cell under test is
+ * compared with the mean power of the training cells, i.e. the cells of the
+ * (2 (guard + train) + 1)^2 square around it minus the (2 guard + 1)^2 guard
+ * square, clipped at the map edge; detection when
+ * z^2 > alpha * mean, alpha = N (pfa^(-1/N) - 1) for N training cells (the
+ * textbook CA-CFAR factor for exponentially distributed noise power). */
+int orc_cacfar(const double* z, int P, int Q, int guard, int train, double pfa, unsigned char* det) {
+  int count = 0;
+  int R = guard + train;
+  for (int p = 0; p < P; ++p)
+    for (int q = 0; q < Q; ++q) {
+      double s = 0.0;
+      int n = 0;
+      for (int dp = -R; dp <= R; ++dp)
+        for (int dq = -R; dq <= R; ++dq) {
+          if (dp >= -guard && dp <= guard && dq >= -guard && dq <= guard) continue;
+          int pp = p + dp, qq = q + dq;
+          if (pp < 0 || pp >= P || qq < 0 || qq >= Q) continue;
+          s += z[pp * Q + qq] * z[pp * Q + qq];
+          ++n;
+        }
+      double alpha = (double)n * (pow(pfa, -1.0 / (double)n) - 1.0);
+      double c = z[p * Q + q] * z[p * Q + q];
+      unsigned char d = n > 0 && c > alpha * (s / (double)n);
+      det[p * Q + q] = d;
+      count += d;
+    }
+  return count;
+}
+
+/* Fraction of distinct target cells with a detection within +-1 cell
+ * (Sec. V-B: AP = N_cd / N, without the clustering step). */
+double orc_detect_rate(const unsigned char* det, int P, int Q, const int* bins, int nb) {
+  int hit = 0, cnt = 0;
+  for (int o = 0; o < nb; ++o) {
+    int dup = 0;
+    for (int k = 0; k < o; ++k) dup |= bins[2 * k] == bins[2 * o] && bins[2 * k + 1] == bins[2 * o + 1];
+    if (dup) continue;
+    ++cnt;
+    int found = 0;
+    for (int dp = -1; dp <= 1; ++dp)
+      for (int dq = -1; dq <= 1; ++dq) {
+        int pp = bins[2 * o] + dp, qq = bins[2 * o + 1] + dq;
+        if (pp >= 0 && pp < P && qq >= 0 && qq < Q && det[pp * Q + qq]) found = 1;
+      }
+    hit += found;
+  }
+  return cnt ? (double)hit / cnt : NAN;
+}

@@ -130,6 +130,13 @@ double orc_sinr_db(const double* z, int P, int Q, const int* bins, int nb,
 double orc_evm(const double* clean, const double* est, int P, int Q,
                const int* bins, int nb);
 
+/* CA-CFAR detections det[P][Q] (0/1) on map z; returns their number. */
+int orc_cacfar(const double* z, int P, int Q, int guard, int train, double pfa,
+               unsigned char* det);
+/* Fraction of distinct target cells with a detection within +-1 cell. */
+double orc_detect_rate(const unsigned char* det, int P, int Q, const int* bins,
+                       int nb);
+
 #ifdef __cplusplus
 }
 #endif

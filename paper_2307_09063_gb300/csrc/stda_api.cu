@@ -702,4 +702,20 @@ stda_status stda_generate(const stda_gen_config* g, uint64_t seed, uint64_t cid,
   return STDA_OK;
 }
 
+stda_status stda_metrics(const void* maps, const void* clean, int bf16, const int* bins, const int* ntgt, int B,
+                         int H, int W, int guard, int cfar_guard, int cfar_train, double pfa, double* sinr,
+                         double* evm, float* det_rate, unsigned char* det, cudaStream_t st) {
+  if (B < 0 || H <= 0 || W <= 0 || guard < 0 || cfar_guard < 0 || cfar_train < 1 || !(pfa > 0.0 && pfa < 1.0))
+    return STDA_ERR_INVALID_ARG;
+  if (B == 0) return STDA_OK;
+  if (!maps || !bins || !ntgt || (evm && !clean)) return STDA_ERR_INVALID_ARG;
+  cudaError_t e = stda::metrics(maps, clean, bf16, bins, ntgt, B, H, W, guard, cfar_guard, cfar_train, pfa, sinr,
+                                evm, det_rate, det, st);
+  if (e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? STDA_ERR_OOM : STDA_ERR_CUDA;
+  }
+  return STDA_OK;
+}
+
 }  // extern "C"

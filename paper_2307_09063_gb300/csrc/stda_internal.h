@@ -84,6 +84,11 @@ size_t scratch_bytes(int B, int H, int W, size_t elem);
 void scratch_carve(void* base, int B, int H, int W, size_t elem,
                    FwdScratch* s);
 
+// Evaluation of denoised maps (SINR, EVM, CA-CFAR).
+cudaError_t metrics(const void* maps, const void* clean, int bf16, const int* bins, const int* ntgt, int B, int H,
+                    int W, int guard, int cfar_guard, int cfar_train, double pfa, double* sinr, double* evm,
+                    float* det_rate, unsigned char* det, cudaStream_t st);
+
 // Generator.
 cudaError_t generate(const stda_gen_config* g, uint64_t seed, uint64_t cid,
                      int w0, int B, int bf16, void* noisy, void* clean,

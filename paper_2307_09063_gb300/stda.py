@@ -66,6 +66,9 @@ def lib():
         L.stda_last_error.argtypes = [_VP]
         L.stda_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, _VP]
+        L.stda_metrics.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP,
+                                   _VP]
         L.stda_submit.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]
         L.stda_flush.argtypes = [_VP, _VP]
         L.stda_serve_close.argtypes = [_VP, ctypes.c_int, _VP]
@@ -310,3 +313,24 @@ def _autograd_function():
 def stda_apply(x, params, ctx):
     """Differentiable application of the denoiser (see STDAFunction)."""
     return _autograd_function().apply(x, params, ctx)
+
+
+def metrics(maps, bins, ntgt, clean=None, guard=2, cfar_guard=2, cfar_train=4, pfa=1e-3, want_det=False,
+            stream=None):
+    """stda_metrics on CUDA tensors maps / clean [B][(1)][H][W] (float or
+    bf16), bins [B][16][2], ntgt [B]: (sinr [B] f64, evm [B] f64 | None,
+    detection rate [B] f32, detections [B][H][W] u8 | None)."""
+    import torch
+
+    B, H, W = maps.shape[0], maps.shape[-2], maps.shape[-1]
+    dev = maps.device
+    bf16 = int(maps.dtype == torch.bfloat16)
+    sinr = torch.empty(B, dtype=torch.float64, device=dev)
+    evm = torch.empty(B, dtype=torch.float64, device=dev) if clean is not None else None
+    rate = torch.empty(B, dtype=torch.float32, device=dev)
+    det = torch.empty((B, H, W), dtype=torch.uint8, device=dev) if want_det else None
+    st = lib().stda_metrics(_ptr(maps), _ptr(clean), bf16, _ptr(bins), _ptr(ntgt), B, H, W, guard, cfar_guard,
+                            cfar_train, pfa, _ptr(sinr), _ptr(evm), _ptr(rate), _ptr(det), _stream(stream))
+    if st != OK:
+        raise StdaError(st, lib().stda_status_string(st).decode())
+    return sinr, evm, rate, det

@@ -345,3 +345,26 @@ def test_output_is_not_degenerate(weights):
     z = O.forward(*weights, noisy.astype(np.float32))
     assert z.std() >= 0.05
     assert np.mean((z > 0.05) & (z < 0.95)) >= 0.5
+
+
+# ------------------------------------------------------------------ CA-CFAR
+def test_cacfar_closed_forms():
+    """A single bright cell on a constant floor is the only detection; a
+    constant map has none (every cell equals its training mean, and alpha >
+    1); the CA-CFAR factor is N (pfa^(-1/N) - 1)."""
+    z = np.full((24, 20), 0.1)
+    det, n = O.cacfar(z, 2, 4, 1e-3)
+    assert n == 0
+    z[10, 7] = 1.0
+    det, n = O.cacfar(z, 2, 4, 1e-3)
+    assert n == 1 and det[10, 7] == 1
+    # threshold closed form: interior cell, N = 13^2 - 5^2 = 144 training cells
+    N = 144
+    alpha = N * (1e-3 ** (-1.0 / N) - 1.0)
+    z2 = np.full((24, 20), 0.1)
+    z2[10, 7] = 0.1 * np.sqrt(alpha) * 1.001
+    assert O.cacfar(z2, 2, 4, 1e-3)[0][10, 7] == 1
+    z2[10, 7] = 0.1 * np.sqrt(alpha) * 0.999
+    assert O.cacfar(z2, 2, 4, 1e-3)[0][10, 7] == 0
+    bins = np.array([[10, 7], [3, 3], [10, 7]])
+    assert O.detect_rate(det, bins) == 0.5
