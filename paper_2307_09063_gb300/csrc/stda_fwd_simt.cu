@@ -16,6 +16,8 @@
 #include "stda_internal.h"
 #include "stda_tc.h"
 
+#include <algorithm>
+
 namespace stda {
 namespace {
 
@@ -538,11 +540,66 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
   return cudaGetLastError();
 }
 
+// Output module for bf16 maps: the ECA weights of decoder block 3 are folded
+// into the conv weights of each window (the conv is linear in its input), the
+// 72 weights live in registers, and each thread computes four horizontally
+// adjacent pixels from the 3 x 6 neighbourhood read straight from global
+// memory (16 bytes = 8 channels per pixel; neighbouring threads share rows
+// through L1).
+__global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a) {
+  __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
+  __shared__ float s_w[72];
+  const int b = blockIdx.y, H = a.H, W = a.W, W4 = W / 4;
+  eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_tmp, s_g, s_s);
+  for (int i = threadIdx.x; i < 72; i += blockDim.x) s_w[i] = a.w.out_w[i] * s_s[i & 7];
+  __syncthreads();
+  float wr[72];
+#pragma unroll
+  for (int i = 0; i < 72; ++i) wr[i] = s_w[i];
+  const float bias = a.w.out_b[0];
+  const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
+  for (int strip = blockIdx.x * blockDim.x + threadIdx.x; strip < H * W4; strip += gridDim.x * blockDim.x) {
+    const int y = strip / W4, x0 = (strip % W4) * 4;
+    float z[4] = {bias, bias, bias, bias};
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      const int yy = y + dy - 1;
+      if (yy < 0 || yy >= H) continue;
+#pragma unroll
+      for (int cx = 0; cx < 6; ++cx) {
+        const int xx = x0 + cx - 1;
+        if (xx < 0 || xx >= W) continue;
+        uint4 u = *(const uint4*)(A + ((size_t)yy * W + xx) * 8);
+        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
+        float f[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float2 t = __bfloat1622float2(hv[k]);
+          f[2 * k] = t.x;
+          f[2 * k + 1] = t.y;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int kx = cx - j;
+          if (kx < 0 || kx > 2) continue;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) z[j] += wr[(dy * 3 + kx) * 8 + c] * f[c];
+        }
+      }
+    }
+    __nv_bfloat16 o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = __float2bfloat16_rn(1.f / (1.f + expf(-z[j])));
+    *(uint2*)(a.out + ((size_t)b * H + y) * W + x0) = *(const uint2*)o;
+  }
+}
+
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
                             __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook) {
   OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
+  const int strips = H * (W / 4);
   hook->begin(K_OUT, st);
-  k_out<__nv_bfloat16><<<dim3(cdiv(W, kOutTX), cdiv(H, kOutTY), B), kThreads, 0, st>>>(a);
+  k_out_bf16<<<dim3(std::min(cdiv(strips, kThreads), 64), B), kThreads, 0, st>>>(a);
   hook->end(st);
   return cudaGetLastError();
 }

@@ -25,6 +25,8 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <tuple>
 
@@ -170,34 +172,31 @@ __device__ __forceinline__ void warp_sum_to(float v, float* dst) {
 // ks[(a % nph) * nsteps ...] for the main branch (a < nph) and the same
 // table for the residual branch (a >= nph).
 template <bool F8>
-__device__ void issue_mmas(uint32_t tmem, const KStep* ks, int nsteps, int nph, int NP, int ntile, int m_lo,
-                           int WP, int PIXA, int terms, uint32_t a_lo_off, uint32_t b_lo_off, uint32_t x1_base,
+__device__ void issue_tile(uint32_t d_base, const KStep* ks, int nsteps, int nph, int NP, int m0, int WP,
+                           int PIXA, int terms, uint32_t a_lo_off, uint32_t b_lo_off, uint32_t x1_base,
                            uint32_t x0_base, uint32_t wm_base, uint32_t wr_base) {
   const uint32_t idesc = F8 ? idesc_e4m3(128, NP) : idesc_bf16(128, NP);
   const uint32_t wstep = 2u * NP * 16u;  // bytes per packed K-step
-  for (int i = 0; i < ntile; ++i) {
-    int m0 = m_lo + 128 * i;
-    for (int a = 0; a < 2 * nph; ++a) {
-      bool res = a >= nph;
-      int ph = res ? a - nph : a;
-      uint32_t xb = res ? x0_base : x1_base, wb = res ? wr_base : wm_base;
-      uint32_t d = tmem + (uint32_t)((i * 2 * nph + a) * NP);
-      for (int j = 0; j < nsteps; ++j) {
-        KStep k = ks[ph * nsteps + j];
-        int p0 = k.pl0 * PIXA + m0 + k.dr0 * WP + k.dc0;
-        int p1 = k.pl1 * PIXA + m0 + k.dr1 * WP + k.dc1;
-        uint32_t aa = xb + (uint32_t)p0 * 16u, lbo = (uint32_t)(p1 - p0) * 16u;
-        uint32_t bb = wb + (uint32_t)(ph * nsteps + j) * wstep;
-        if (F8) {
-          // two-term operands: hi*hi + lo*hi + hi*lo
-          mma_f8(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
-          if (terms == 2) {
-            mma_f8(d, desc(aa + a_lo_off, lbo, 128), desc(bb, NP * 16u, 128), idesc, 1);
-            mma_f8(d, desc(aa, lbo, 128), desc(bb + b_lo_off, NP * 16u, 128), idesc, 1);
-          }
-        } else {
-          mma_bf16(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+  for (int a = 0; a < 2 * nph; ++a) {
+    bool res = a >= nph;
+    int ph = res ? a - nph : a;
+    uint32_t xb = res ? x0_base : x1_base, wb = res ? wr_base : wm_base;
+    uint32_t d = d_base + (uint32_t)(a * NP);
+    for (int j = 0; j < nsteps; ++j) {
+      KStep k = ks[ph * nsteps + j];
+      int p0 = k.pl0 * PIXA + m0 + k.dr0 * WP + k.dc0;
+      int p1 = k.pl1 * PIXA + m0 + k.dr1 * WP + k.dc1;
+      uint32_t aa = xb + (uint32_t)p0 * 16u, lbo = (uint32_t)(p1 - p0) * 16u;
+      uint32_t bb = wb + (uint32_t)(ph * nsteps + j) * wstep;
+      if (F8) {
+        // two-term operands: hi*hi + lo*hi + hi*lo
+        mma_f8(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+        if (terms == 2) {
+          mma_f8(d, desc(aa + a_lo_off, lbo, 128), desc(bb, NP * 16u, 128), idesc, 1);
+          mma_f8(d, desc(aa, lbo, 128), desc(bb + b_lo_off, NP * 16u, 128), idesc, 1);
         }
+      } else {
+        mma_bf16(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
       }
     }
   }
@@ -227,7 +226,8 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
 // Misc area: [0, 512) K-step table, [512, 1024) ECA g / s (input),
 // [1024, 1536) ECA s (skip), [1536, 4096) stage-1 weights + bias,
 // [4096, 5120) stem weights + bias, [5120, 9216) per-warp channel sums
-// (up to 16 warps), [9216] mbarrier, [9224] TMEM slot.
+// (up to 16 warps), [9216, 9248) mbarriers (one per TMEM tile buffer),
+// [9248] TMEM slot.
 struct Misc {
   KStep* ks;
   float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red;
@@ -244,7 +244,7 @@ struct Misc {
     stb = stw + 216;
     red = (float*)(p + 5120);
     bar = (uint64_t*)(p + 9216);
-    tslot = (uint32_t*)(p + 9224);
+    tslot = (uint32_t*)(p + 9248);
   }
 };
 
@@ -291,28 +291,42 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   unsigned char* x0 = sm + L.off_x0;
   unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.y, band = blockIdx.x, TY = a.band;
+  const int TY = a.band;
   const int h = a.h, w = a.w, ho = h / 2, wo = w / 2;
-  const int oy0 = band * TY, WP = a.WP, PIXA = a.PIXA;
+  const int WP = a.WP, PIXA = a.PIXA;
   // 16-byte pixel of plane pl
   auto px = [&](unsigned char* base, int pl, int p) { return (uint4*)(base + ((size_t)pl * PIXA + p) * 16); };
 
+  // once per CTA: weights, tables, barrier, tensor memory
   if (tid == 0) {
-    mbar_init(M.bar, 1);
+    for (int k = 0; k < a.nbuf; ++k) mbar_init(M.bar + k, 1);
     mbar_fence_init();
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
   copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
-  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
   for (int i = tid; i < nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
   if (STEM) {
     for (int i = tid; i < 216; i += blockDim.x) M.stw[i] = a.stem_w[i];
     for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
-  } else {
-    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
   }
+  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *M.tslot;
+  uint32_t phases = 0;  // bit k: parity of buffer k's next completion
+  const int items = a.tiles_per_window * a.nwin;
+  bool failed = false;
+
+  // persistent loop over (window, band) items
+  for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+  const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
+  const int oy0 = band * TY;
+  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
+  if (!STEM)
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
@@ -427,63 +441,75 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
     }
   }
   fence_proxy_async();
-  // TMEM is taken only now, so that co-resident CTAs stage while this one
-  // waits for columns
-  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = *M.tslot;
   const int m_lo = WP + 1;
-  // 3. stage 2 on the tensor cores
-  if (tid == 0) {
-    issue_mmas<F8>(tmem, M.ks, nsteps, 1, NP, a.ntile, m_lo, WP, PIXA, T, (uint32_t)lo_off,
-                   (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0), smem_u32(sm + L.off_wm),
-                   smem_u32(sm + L.off_wr));
-    commit(M.bar);
-  }
-  const bool ok = mbar_wait(M.bar, 0);
-  fence_after_sync();
-  if (!ok) {
-    if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
-    mbar_wait(M.bar, 0);  // bounded: let issued MMAs drain before TMEM is freed
-  } else {
-    // 4. epilogue: warps w, w + 4, ... share TMEM lanes; they take alternate tiles
-    for (int i = warp >> 2; i < a.ntile; i += (int)(blockDim.x >> 7)) {
-      int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-      int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
-      bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
-      __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
+  // 3. stage 2 on the tensor cores, 128-row tiles through nbuf TMEM buffers;
+  // 4. epilogue: warp group g drains buffer g (warps g*4 .. g*4+3 cover the
+  // 128 TMEM lanes)
+  const int cpt = 2 * NP;  // TMEM columns per tile
+  for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
+    if (tid == 0)
+      for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
+        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.ks, nsteps, 1, NP, m_lo + 128 * (t0 + k), WP, PIXA, T,
+                       (uint32_t)lo_off, (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0),
+                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+        commit(M.bar + k);
+      }
+    const int g = warp >> 2, i = t0 + g;
+    bool ok = true;
+    if (g < a.nbuf && i < a.ntile) {
+      ok = mbar_wait(M.bar + g, (phases >> g) & 1u);
+      fence_after_sync();
+      if (ok) {
+        const uint32_t col = (uint32_t)(g * cpt);
+        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+        int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
+        bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
+        __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
 #pragma unroll
-      for (int c = 0; c < CO; c += 16) {
-        float mv[16], rv[16];
-        ld16(lane_addr(tmem, warp, i * 2 * NP + c), mv);
-        ld16(lane_addr(tmem, warp, i * 2 * NP + NP + c), rv);
-        ld_wait();
-        float o[16];
+        for (int c = 0; c < CO; c += 16) {
+          float mv[16], rv[16];
+          ld16(lane_addr(tmem, warp, col + c), mv);
+          ld16(lane_addr(tmem, warp, col + NP + c), rv);
+          ld_wait();
+          float o[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
-                             a.rb[c + j])
-                       : 0.f;
-        if (valid) {
-          *(uint4*)(dst + c) = f32_to_bf16x8(o);
-          *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
+          for (int j = 0; j < 16; ++j)
+            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
+                               a.rb[c + j])
+                         : 0.f;
+          if (valid) {
+            *(uint4*)(dst + c) = f32_to_bf16x8(o);
+            *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) warp_sum_to(o[j], &M.red[warp * CO + c + j]);
         }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) warp_sum_to(o[j], &M.red[warp * CO + c + j]);
       }
     }
+    for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) phases ^= 1u << k;
+    fence_before_sync();
+    // CTA-wide agreement on the bounded waits; on a timeout the CTA records
+    // the error, lets its MMAs drain (bounded) and stops
+    failed = __syncthreads_or(!ok);
+    fence_after_sync();
   }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
-  float* part = a.part + ((size_t)b * gridDim.x + band) * CO;
+  if (failed) {
+    if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
+    for (int k = 0; k < a.nbuf; ++k) mbar_wait(M.bar + k, ((phases >> k) & 1u) ^ 1u);
+    break;
+  }
+  float* part = a.part + ((size_t)b * a.tiles_per_window + band) * CO;
   for (int c = tid; c < CO; c += blockDim.x) {
     float s = 0.f;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += M.red[k * CO + c];
     part[c] = s;
   }
+  __syncthreads();
+  }  // item loop
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
 // ---------------------------------------------------------------- decoder
@@ -499,22 +525,34 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   unsigned char* x0 = sm + L.off_x0;
   unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.y, band = blockIdx.x, TA = a.band;
+  const int TA = a.band;
   const int h = a.h, w = a.w, Ho = 2 * h, Wo = 2 * w;
-  const int a0 = band * TA, WP = a.WP, PIXA = a.PIXA;
+  const int WP = a.WP, PIXA = a.PIXA;
   auto px = [&](unsigned char* base, int g, int p) { return (uint4*)(base + ((size_t)g * PIXA + p) * 16); };
 
   if (tid == 0) {
-    mbar_init(M.bar, 1);
+    for (int k = 0; k < a.nbuf; ++k) mbar_init(M.bar + k, 1);
     mbar_fence_init();
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
   copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
-  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
   for (int i = tid; i < 4 * nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
+  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *M.tslot;
+  uint32_t phases = 0;  // bit k: parity of buffer k's next completion
+  const int items = a.tiles_per_window * a.nwin;
+  bool failed = false;
   const float inv_n = 1.f / (float)(h * w);
+
+  for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+  const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
+  const int a0 = band * TA;
+  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
   eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.red, M.g, M.sa);
   if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.red, M.g, M.ss);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
@@ -588,59 +626,70 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
     }
   }
   fence_proxy_async();
-  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = *M.tslot;
   const int m_lo = 2 * WP + 2;
-  if (tid == 0) {
-    issue_mmas<F8>(tmem, M.ks, nsteps, 4, NP, a.ntile, m_lo, WP, PIXA, T, (uint32_t)lo_off,
-                   (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0), smem_u32(sm + L.off_wm),
-                   smem_u32(sm + L.off_wr));
-    commit(M.bar);
-  }
-  const bool ok = mbar_wait(M.bar, 0);
-  fence_after_sync();
-  if (!ok) {
-    if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
-    mbar_wait(M.bar, 0);  // bounded: let issued MMAs drain before TMEM is freed
-  } else {
-    for (int i = warp >> 2; i < a.ntile; i += (int)(blockDim.x >> 7)) {
-      int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-      int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
-      bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
+  const int cpt = 8 * NP;  // TMEM columns per tile: 4 phases x (main, residual)
+  for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
+    if (tid == 0)
+      for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
+        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.ks, nsteps, 4, NP, m_lo + 128 * (t0 + k), WP, PIXA, T,
+                       (uint32_t)lo_off, (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0),
+                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+        commit(M.bar + k);
+      }
+    const int g = warp >> 2, i = t0 + g;
+    bool ok = true;
+    if (g < a.nbuf && i < a.ntile) {
+      ok = mbar_wait(M.bar + g, (phases >> g) & 1u);
+      fence_after_sync();
+      if (ok) {
+        const uint32_t col = (uint32_t)(g * cpt);
+        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+        int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
+        bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
 #pragma unroll 1
-      for (int ph = 0; ph < 4; ++ph) {
-        int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
-        __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
+        for (int ph = 0; ph < 4; ++ph) {
+          int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
+          __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
 #pragma unroll
-        for (int cc = 0; cc < CO; cc += 8) {
-          float mv[8], rv[8], o[8];
-          ld8(lane_addr(tmem, warp, (i * 8 + ph) * NP + cc), mv);
-          ld8(lane_addr(tmem, warp, (i * 8 + 4 + ph) * NP + cc), rv);
-          ld_wait();
+          for (int cc = 0; cc < CO; cc += 8) {
+            float mv[8], rv[8], o[8];
+            ld8(lane_addr(tmem, warp, col + ph * NP + cc), mv);
+            ld8(lane_addr(tmem, warp, col + (4 + ph) * NP + cc), rv);
+            ld_wait();
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
-                               a.b2[cc + j], a.rb[cc + j])
-                         : 0.f;
-          if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
+            for (int j = 0; j < 8; ++j)
+              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
+                                 a.b2[cc + j], a.rb[cc + j])
+                           : 0.f;
+            if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) warp_sum_to(o[j], &M.red[warp * CO + cc + j]);
+            for (int j = 0; j < 8; ++j) warp_sum_to(o[j], &M.red[warp * CO + cc + j]);
+          }
         }
       }
     }
+    for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) phases ^= 1u << k;
+    fence_before_sync();
+    failed = __syncthreads_or(!ok);
+    fence_after_sync();
   }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
-  float* part = a.part + ((size_t)b * gridDim.x + band) * CO;
+  if (failed) {
+    if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
+    for (int k = 0; k < a.nbuf; ++k) mbar_wait(M.bar + k, ((phases >> k) & 1u) ^ 1u);
+    break;
+  }
+  float* part = a.part + ((size_t)b * a.tiles_per_window + band) * CO;
   for (int c = tid; c < CO; c += blockDim.x) {
     float s = 0.f;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += M.red[k * CO + c];
     part[c] = s;
   }
+  __syncthreads();
+  }  // item loop
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
 uint32_t pow2_cols(int cols) {
@@ -665,16 +714,41 @@ int steps_per_acc(int b, bool f8) {
 // Two passes: first a band that lets two CTAs share an SM (shared memory
 // <= half, TMEM <= 256 columns), then any band that fits.
 struct Geo {
-  int band, ntile, WP, PIXA, smem, threads;
+  int band, ntile, WP, PIXA, smem, threads, nbuf;
   uint32_t cols;
 };
+
+// TMEM tile buffers: as many as warp groups, within the column budget.
+void pick_buffers(Geo& g, int cpt, int budget) {
+  const int groups = g.threads / 128;
+  g.nbuf = 0;
+  for (int k = groups; k >= 1; --k)
+    if ((int)pow2_cols(k * cpt) <= budget) {
+      g.nbuf = k;
+      break;
+    }
+  g.cols = pow2_cols(std::max(g.nbuf, 1) * cpt);
+}
+
+// Tuning override: STDA_TC_BANDS="e1,e2,e3,d1,d2,d3" caps each level's band
+// height (0 = automatic). The geometry rules still apply.
+int band_cap(int b) {
+  static int caps[6] = {-1, -1, -1, -1, -1, -1};
+  if (caps[0] < 0) {
+    for (int& c : caps) c = 0;
+    if (const char* e = getenv("STDA_TC_BANDS")) sscanf(e, "%d,%d,%d,%d,%d,%d", &caps[0], &caps[1], &caps[2],
+                                                        &caps[3], &caps[4], &caps[5]);
+  }
+  return caps[b];
+}
 
 Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
   const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
   const bool stem = b == 0;
   Geo g{};
   for (int pass = 0; pass < 2; ++pass)
-    for (int TY = 8; TY >= 1; TY >>= 1) {
+    for (int TY = 16; TY >= 1; TY >>= 1) {
+      if (band_cap(b) && TY > band_cap(b)) continue;
       g.band = TY;
       g.WP = wo + 2;
       int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
@@ -683,10 +757,9 @@ Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
       g.PIXA = (g.PIXA + 7) / 8 * 8;
       int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
       g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms).total;
-      g.cols = pow2_cols(g.ntile * 2 * CO);
       g.threads = pass == 0 ? 256 : 512;
-      if (pass == 0 ? (g.cols <= 256 && g.smem <= kTcHalfSmem) : (g.ntile * 2 * CO <= 512 && g.smem <= kTcMaxSmem))
-        return g;
+      pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
+      if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
     }
   g.band = 0;
   return g;
@@ -697,7 +770,8 @@ Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
             nsteps = steps_per_acc(b, f8);
   Geo g{};
   for (int pass = 0; pass < 2; ++pass)
-    for (int TA = 8; TA >= 1; TA >>= 1) {
+    for (int TA = 16; TA >= 1; TA >>= 1) {
+      if (band_cap(b) && TA > band_cap(b)) continue;
       g.band = TA;
       g.WP = w + 4;
       int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
@@ -705,20 +779,36 @@ Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
       g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
       g.PIXA = (g.PIXA + 7) / 8 * 8;
       g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0, terms).total;
-      g.cols = pow2_cols(g.ntile * 8 * NP);
       g.threads = pass == 0 ? 256 : 512;
-      if (pass == 0 ? (g.cols <= 256 && g.smem <= kTcHalfSmem) : (g.ntile * 8 * NP <= 512 && g.smem <= kTcMaxSmem))
-        return g;
+      pick_buffers(g, 8 * NP, pass == 0 ? 256 : 512);
+      if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
     }
   g.band = 0;
   return g;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Persistent launch: one CTA per SM (two where the geometry allows), each
+// looping over (window, band) items.
 template <typename K>
 cudaError_t launch(K kern, const Geo& g, int B, const TcArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
   if (e) return e;
-  kern<<<dim3(a.tiles_per_window, B), g.threads, g.smem, st>>>(a);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const int per_sm = g.threads == 256 ? 2 : 1;
+  const long items = (long)a.tiles_per_window * B;
+  const int grid = (int)std::min<long>(items, (long)sm_count() * per_sm);
+  kern<<<grid, g.threads, g.smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -901,6 +991,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.WP = g.WP;
     a.PIXA = g.PIXA;
     a.tmem_cols = g.cols;
+    a.nbuf = g.nbuf;
     a.stem_w = w.stem_w;
     a.stem_b = w.stem_b;
     a.dw = w.blk[l].dw;
@@ -914,6 +1005,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.status = status;
     const int rows = kBlkEnc[l] ? h / 2 : h;
     a.tiles_per_window = cdiv(rows, g.band);
+    a.nwin = B;
     tiles[l] = a.tiles_per_window;
     hook->begin(K_ENC1 + l, st);
     switch (l * 2 + (f8 ? 1 : 0)) {

@@ -51,6 +51,8 @@ struct TcArgs {
   int ntile;      // 128-row GEMM tiles per CTA
   int WP, PIXA;   // plane pitch and pixels per plane
   int tiles_per_window;
+  int nwin;  // windows in the batch (items = windows x bands)
+  int nbuf;  // TMEM tile buffers (1 .. warp groups)
   int nsteps;
   uint32_t tmem_cols;
   const float *stem_w, *stem_b, *dw, *dwb, *b2, *rb;
