@@ -546,7 +546,7 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
 // adjacent pixels from the 3 x 6 neighbourhood read straight from global
 // memory (16 bytes = 8 channels per pixel; neighbouring threads share rows
 // through L1).
-__global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a) {
+__global__ void __launch_bounds__(kThreads, 2) k_out_bf16(OutArgs<__nv_bfloat16> a) {
   __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
   __shared__ float s_w[72];
   const int b = blockIdx.y, H = a.H, W = a.W, W4 = W / 4;
@@ -599,7 +599,8 @@ cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float*
   OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
   const int strips = H * (W / 4);
   hook->begin(K_OUT, st);
-  k_out_bf16<<<dim3(std::min(cdiv(strips, kThreads), 64), B), kThreads, 0, st>>>(a);
+  // about eight strips per thread: the per-CTA ECA reduction is amortised
+  k_out_bf16<<<dim3(std::max(1, cdiv(strips, kThreads * 8)), B), kThreads, 0, st>>>(a);
   hook->end(st);
   return cudaGetLastError();
 }

@@ -57,6 +57,15 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
   return u;
 }
 
+// acc = a * b + acc on a pair of FP32 lanes in one instruction (packed FP32
+// FMA of sm_100-class GPUs; each lane rounds exactly like a scalar FMA).
+__device__ __forceinline__ void ffma2(float2& acc, float2 a, float2 b) {
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%0, %1};\n\tfma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+      : "+f"(acc.x), "+f"(acc.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+}
+
 // A 16-byte pixel of a staged plane: 8 bf16 channels, or 16 E4M3 channels.
 template <bool F8>
 struct Op;
@@ -171,32 +180,56 @@ __device__ __forceinline__ void warp_sum_to(float v, float* dst) {
 // at TMEM column (i * nacc + a) * NP; K-steps of accumulator a are
 // ks[(a % nph) * nsteps ...] for the main branch (a < nph) and the same
 // table for the residual branch (a >= nph).
+// Descriptor table: one entry per (accumulator, K-step), the low words of
+// the A and B shared-memory descriptors for the first tile of an item. The
+// high words (SBO = 128 bytes, version 1) are the same for every operand.
+// Later tiles shift the A start address (16-byte units) by their first
+// pixel; every shifted address is a real operand address below 227 KB, so
+// the 14-bit start field never carries into the LBO field.
+constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);
+
 template <bool F8>
-__device__ void issue_tile(uint32_t d_base, const KStep* ks, int nsteps, int nph, int NP, int m0, int WP,
-                           int PIXA, int terms, uint32_t a_lo_off, uint32_t b_lo_off, uint32_t x1_base,
-                           uint32_t x0_base, uint32_t wm_base, uint32_t wr_base) {
-  const uint32_t idesc = F8 ? idesc_e4m3(128, NP) : idesc_bf16(128, NP);
+__device__ void fill_desc_table(uint2* tab, const KStep* ks, int nsteps, int nph, int NP, int m_lo, int WP,
+                                int PIXA, uint32_t x1_base, uint32_t x0_base, uint32_t wm_base, uint32_t wr_base) {
   const uint32_t wstep = 2u * NP * 16u;  // bytes per packed K-step
-  for (int a = 0; a < 2 * nph; ++a) {
-    bool res = a >= nph;
-    int ph = res ? a - nph : a;
-    uint32_t xb = res ? x0_base : x1_base, wb = res ? wr_base : wm_base;
-    uint32_t d = d_base + (uint32_t)(a * NP);
+  for (int e = threadIdx.x; e < 2 * nph * nsteps; e += blockDim.x) {
+    const int acc = e / nsteps, j = e % nsteps;
+    const bool res = acc >= nph;
+    const int ph = res ? acc - nph : acc;
+    const uint32_t xb = res ? x0_base : x1_base, wb = res ? wr_base : wm_base;
+    const KStep k = ks[ph * nsteps + j];
+    const int p0 = k.pl0 * PIXA + m_lo + k.dr0 * WP + k.dc0;
+    const int p1 = k.pl1 * PIXA + m_lo + k.dr1 * WP + k.dc1;
+    const uint64_t da = desc(xb + (uint32_t)p0 * 16u, (uint32_t)(p1 - p0) * 16u, 128);
+    const uint64_t db = desc(wb + (uint32_t)(ph * nsteps + j) * wstep, NP * 16u, 128);
+    tab[e] = make_uint2((uint32_t)da, (uint32_t)db);
+  }
+}
+
+// Issues the MMAs of one tile: 2 * nph accumulators (main then residual per
+// output phase) of nsteps K-steps each, from the descriptor table. dm is the
+// tile's A shift from the first tile, in 16-byte units (one pixel).
+template <bool F8>
+__device__ __forceinline__ void issue_tile(uint32_t d_base, const uint2* tab, int nsteps, int nph, int NP,
+                                           uint32_t dm, int terms, uint32_t a_lo, uint32_t b_lo) {
+  const uint32_t idesc = F8 ? idesc_e4m3(128, NP) : idesc_bf16(128, NP);
+  const uint64_t hi = (uint64_t)kDescHi << 32;
+  for (int acc = 0; acc < 2 * nph; ++acc) {
+    const uint2* t = tab + acc * nsteps;
+    const uint32_t d = d_base + (uint32_t)(acc * NP);
+#pragma unroll 4
     for (int j = 0; j < nsteps; ++j) {
-      KStep k = ks[ph * nsteps + j];
-      int p0 = k.pl0 * PIXA + m0 + k.dr0 * WP + k.dc0;
-      int p1 = k.pl1 * PIXA + m0 + k.dr1 * WP + k.dc1;
-      uint32_t aa = xb + (uint32_t)p0 * 16u, lbo = (uint32_t)(p1 - p0) * 16u;
-      uint32_t bb = wb + (uint32_t)(ph * nsteps + j) * wstep;
+      const uint2 e = t[j];
+      const uint64_t da = hi | (e.x + dm), db = hi | e.y;
       if (F8) {
         // two-term operands: hi*hi + lo*hi + hi*lo
-        mma_f8(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+        mma_f8(d, da, db, idesc, j > 0);
         if (terms == 2) {
-          mma_f8(d, desc(aa + a_lo_off, lbo, 128), desc(bb, NP * 16u, 128), idesc, 1);
-          mma_f8(d, desc(aa, lbo, 128), desc(bb + b_lo_off, NP * 16u, 128), idesc, 1);
+          mma_f8(d, hi | (e.x + dm + a_lo), db, idesc, 1);
+          mma_f8(d, da, hi | (e.y + b_lo), idesc, 1);
         }
       } else {
-        mma_bf16(d, desc(aa, lbo, 128), desc(bb, NP * 16u, 128), idesc, j > 0);
+        mma_bf16(d, da, db, idesc, j > 0);
       }
     }
   }
@@ -211,7 +244,7 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
                                             int terms = 1) {
   Smem s;
   s.wbytes = terms * nsteps_total * 2 * NP * 16;
-  s.planes_bytes = terms * nplanes * PIXA * 16;
+  s.planes_bytes = (terms * nplanes * PIXA * 16 + 127) / 128 * 128;
   s.in_bytes = (in_bytes + 127) / 128 * 128;
   s.off_wm = 0;
   s.off_wr = s.wbytes;
@@ -223,28 +256,28 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
   return s;
 }
 
-// Misc area: [0, 512) K-step table, [512, 1024) ECA g / s (input),
-// [1024, 1536) ECA s (skip), [1536, 4096) stage-1 weights + bias,
-// [4096, 5120) stem weights + bias, [5120, 9216) per-warp channel sums
-// (up to 16 warps), [9216, 9248) mbarriers (one per TMEM tile buffer),
-// [9248] TMEM slot.
+// Misc area: [0, 1024) descriptor table (up to 128 entries), [1024, 1536)
+// ECA g / s (input), [1536, 2048) ECA s (skip), [2048, 4608) stage-1 weights
+// + bias, [4608, 5632) stem weights + bias, [5632, 9728) per-warp channel
+// sums (up to 16 warps), [9728, 9760) mbarriers (one per TMEM tile buffer),
+// [9760] TMEM slot.
 struct Misc {
-  KStep* ks;
+  uint2* dtab;
   float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red;
   uint64_t* bar;
   uint32_t* tslot;
   __device__ Misc(unsigned char* p, int CI) {
-    ks = (KStep*)p;
-    g = (float*)(p + 512);
+    dtab = (uint2*)p;
+    g = (float*)(p + 1024);
     sa = g + 64;
-    ss = (float*)(p + 1024);
-    dw = (float*)(p + 1536);
+    ss = (float*)(p + 1536);
+    dw = (float*)(p + 2048);
     dwb = dw + 9 * CI;
-    stw = (float*)(p + 4096);
+    stw = (float*)(p + 4608);
     stb = stw + 216;
-    red = (float*)(p + 5120);
-    bar = (uint64_t*)(p + 9216);
-    tslot = (uint32_t*)(p + 9248);
+    red = (float*)(p + 5632);
+    bar = (uint64_t*)(p + 9728);
+    tslot = (uint32_t*)(p + 9760);
   }
 };
 
@@ -304,7 +337,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
   copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
-  for (int i = tid; i < nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
+  const int m_lo = WP + 1;
+  fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, 1, NP, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
+                      smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
   if (STEM) {
@@ -346,42 +381,49 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
         },
         [&](int i, uint4 v) { *(uint4*)(sin + (size_t)i * 8) = v; });
     __syncthreads();
-    // stem conv 3 -> 8: two horizontally adjacent positions per thread share
-    // the weight loads
-    const int w2 = w / 2;
-    for (int i = tid; i < (y_hi - y_lo + 1) * w2; i += blockDim.x) {
-      const int y = y_lo + i / w2, x = 2 * (i % w2);
-      float acc0[8], acc1[8];
+    // stem conv 3 -> 8: four horizontally adjacent positions per thread share
+    // the weight loads; channel pairs go through packed FP32 FMAs
+    const int w4 = w / 4;
+    for (int i = tid; i < (y_hi - y_lo + 1) * w4; i += blockDim.x) {
+      const int y = y_lo + i / w4, x = 4 * (i % w4);
+      float2 acc[4][4];
 #pragma unroll
-      for (int o = 0; o < 8; ++o) acc0[o] = acc1[o] = M.stb[o];
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[p][k] = make_float2(M.stb[2 * k], M.stb[2 * k + 1]);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
           const __nv_bfloat16* row = sin + (c * RI + y - yi0 + ky - 1) * CW + x + 7;
-          float v[4];
+          float v[6];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[q] = __bfloat162float(row[q]);
+          for (int q = 0; q < 6; ++q) v[q] = __bfloat162float(row[q]);
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
             const float4 wa = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8];
             const float4 wb = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8 + 4];
-            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const float2 wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                  make_float2(wb.z, wb.w)};
 #pragma unroll
-            for (int o = 0; o < 8; ++o) {
-              acc0[o] += v[kx] * wv[o];
-              acc1[o] += v[kx + 1] * wv[o];
+            for (int p = 0; p < 4; ++p) {
+              const float2 vv = make_float2(v[p + kx], v[p + kx]);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) ffma2(acc[p][k], vv, wv[k]);
             }
           }
         }
+      const int prow = ((y >> 1) - oy0 + 1) * WP, pl = (y & 1) * 2;
 #pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        acc0[o] = fmaxf(acc0[o], 0.f);
-        acc1[o] = fmaxf(acc1[o], 0.f);
+      for (int p = 0; p < 4; ++p) {
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          o[2 * k] = fmaxf(acc[p][k].x, 0.f);
+          o[2 * k + 1] = fmaxf(acc[p][k].y, 0.f);
+        }
+        store_px<F8>(px(x0, pl + (p & 1), prow + ((x + p) >> 1) + 1), o, T, lo_off);
       }
-      const int p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1, pl = (y & 1) * 2;
-      store_px<F8>(px(x0, pl, p), acc0, T, lo_off);
-      store_px<F8>(px(x0, pl + 1, p), acc1, T, lo_off);
     }
   } else {
     // the band's rows are contiguous in NHWC: item i is pixel i / G, group i % G
@@ -415,9 +457,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
     const int y1_lo = max(0, 2 * oy0 - 1), y1_hi = min(h - 1, 2 * oy0 + 2 * TY - 1);
     for (int i = tid; i < (y1_hi - y1_lo + 1) * w * G; i += blockDim.x) {
       int g = i % G, pos = i / G, y = y1_lo + pos / w, x = pos % w;
-      float acc[CG];
+      float2 acc2[CG / 2];
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] = M.dwb[g * CG + c];
+      for (int c = 0; c < CG / 2; ++c) acc2[c] = make_float2(M.dwb[g * CG + 2 * c], M.dwb[g * CG + 2 * c + 1]);
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
@@ -428,14 +470,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
 #pragma unroll
         for (int q = 0; q < CG / 4; ++q) {
           float4 wv = wt[q];
-          acc[4 * q] += wv.x * f[4 * q];
-          acc[4 * q + 1] += wv.y * f[4 * q + 1];
-          acc[4 * q + 2] += wv.z * f[4 * q + 2];
-          acc[4 * q + 3] += wv.w * f[4 * q + 3];
+          ffma2(acc2[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+          ffma2(acc2[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
         }
       }
+      float acc[CG];
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] = fmaxf(acc[c], 0.f);
+      for (int c = 0; c < CG / 2; ++c) {
+        acc[2 * c] = fmaxf(acc2[c].x, 0.f);
+        acc[2 * c + 1] = fmaxf(acc2[c].y, 0.f);
+      }
       int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
       store_px<F8>(px(x1, pl, p), acc, T, lo_off);
     }
@@ -452,9 +496,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
     if (tid == 0)
       for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
-        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.ks, nsteps, 1, NP, m_lo + 128 * (t0 + k), WP, PIXA, T,
-                       (uint32_t)lo_off, (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0),
-                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.dtab, nsteps, 1, NP, (uint32_t)(128 * (t0 + k)), T,
+                       (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4);
         commit(M.bar + k);
       }
     const int g = warp >> 2, i = t0 + g;
@@ -536,7 +579,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
   copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
-  for (int i = tid; i < 4 * nsteps; i += blockDim.x) M.ks[i] = a.L.ks[i];
+  const int m_lo = 2 * WP + 2;
+  fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, 4, NP, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
+                      smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
   if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
@@ -603,9 +648,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
     for (int i = tid; i < (r_hi - r_lo + 1) * w * G; i += blockDim.x) {
       int g = i % G, pos = i / G, r = r_lo + pos / w, c = pos % w;
       int p = (r - a0 + 2) * WP + c + 2;
-      float acc[CG];
+      float2 acc2[CG / 2];
 #pragma unroll
-      for (int k = 0; k < CG; ++k) acc[k] = M.dwb[g * CG + k];
+      for (int k = 0; k < CG / 2; ++k) acc2[k] = make_float2(M.dwb[g * CG + 2 * k], M.dwb[g * CG + 2 * k + 1]);
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         float f[CG];
@@ -614,14 +659,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
 #pragma unroll
         for (int q = 0; q < CG / 4; ++q) {
           float4 wv = wt[q];
-          acc[4 * q] += wv.x * f[4 * q];
-          acc[4 * q + 1] += wv.y * f[4 * q + 1];
-          acc[4 * q + 2] += wv.z * f[4 * q + 2];
-          acc[4 * q + 3] += wv.w * f[4 * q + 3];
+          ffma2(acc2[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+          ffma2(acc2[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
         }
       }
+      float acc[CG];
 #pragma unroll
-      for (int k = 0; k < CG; ++k) acc[k] = fmaxf(acc[k], 0.f);
+      for (int k = 0; k < CG / 2; ++k) {
+        acc[2 * k] = fmaxf(acc2[k].x, 0.f);
+        acc[2 * k + 1] = fmaxf(acc2[k].y, 0.f);
+      }
       store_px<F8>(px(x1, g, p), acc, T, lo_off);
     }
   }
@@ -629,14 +676,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const int m_lo = 2 * WP + 2;
   const int cpt = 8 * NP;  // TMEM columns per tile: 4 phases x (main, residual)
   for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
     if (tid == 0)
       for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
-        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.ks, nsteps, 4, NP, m_lo + 128 * (t0 + k), WP, PIXA, T,
-                       (uint32_t)lo_off, (uint32_t)(L.wbytes / T), smem_u32(x1), smem_u32(x0),
-                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.dtab, nsteps, 4, NP, (uint32_t)(128 * (t0 + k)), T,
+                       (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4);
         commit(M.bar + k);
       }
     const int g = warp >> 2, i = t0 + g;
@@ -649,25 +694,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
         int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
         bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
+        // channel sums over the four output phases in a fixed order, then one
+        // warp reduction per channel
 #pragma unroll 1
-        for (int ph = 0; ph < 4; ++ph) {
-          int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
-          __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
+        for (int cc = 0; cc < CO; cc += 8) {
+          float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int cc = 0; cc < CO; cc += 8) {
+          for (int ph = 0; ph < 4; ++ph) {
+            int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
+            __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
             float mv[8], rv[8], o[8];
             ld8(lane_addr(tmem, warp, col + ph * NP + cc), mv);
             ld8(lane_addr(tmem, warp, col + (4 + ph) * NP + cc), rv);
             ld_wait();
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < 8; ++j) {
               o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
                                  a.b2[cc + j], a.rb[cc + j])
                            : 0.f;
+              sum[j] += o[j];
+            }
             if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) warp_sum_to(o[j], &M.red[warp * CO + cc + j]);
           }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) warp_sum_to(sum[j], &M.red[warp * CO + cc + j]);
         }
       }
     }
@@ -742,19 +792,30 @@ int band_cap(int b) {
   return caps[b];
 }
 
+// Geometry policy: 0 = prefer two CTAs per SM, then the largest band;
+// 1 = prefer the largest band (either CTA shape). STDA_TC_POLICY overrides.
+int geo_policy() {
+  static int p = -1;
+  if (p < 0) {
+    const char* e = getenv("STDA_TC_POLICY");
+    p = e ? atoi(e) : 0;
+  }
+  return p;
+}
+
 Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
   const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
   const bool stem = b == 0;
   Geo g{};
-  for (int pass = 0; pass < 2; ++pass)
-    for (int TY = 16; TY >= 1; TY >>= 1) {
+  for (int it = 0; it < 10; ++it) {
+      const int pass = geo_policy() ? it % 2 : it / 5, TY = 16 >> (geo_policy() ? it / 2 : it % 5);
       if (band_cap(b) && TY > band_cap(b)) continue;
       g.band = TY;
       g.WP = wo + 2;
       int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8;
+      g.PIXA = (g.PIXA + 7) / 8 * 8 + 1;  // plane stride 16 mod 128 bytes: no bank conflicts
       int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
       g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms).total;
       g.threads = pass == 0 ? 256 : 512;
@@ -769,15 +830,15 @@ Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
   const int CI = kBlkCin[b], CO = CI / 2, G = CI / (f8 ? 16 : 8), NP = CO < 16 ? 16 : CO,
             nsteps = steps_per_acc(b, f8);
   Geo g{};
-  for (int pass = 0; pass < 2; ++pass)
-    for (int TA = 16; TA >= 1; TA >>= 1) {
+  for (int it = 0; it < 10; ++it) {
+      const int pass = geo_policy() ? it % 2 : it / 5, TA = 16 >> (geo_policy() ? it / 2 : it % 5);
       if (band_cap(b) && TA > band_cap(b)) continue;
       g.band = TA;
       g.WP = w + 4;
       int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8;
+      g.PIXA = (g.PIXA + 7) / 8 * 8 + 1;  // plane stride 16 mod 128 bytes: no bank conflicts
       g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0, terms).total;
       g.threads = pass == 0 ? 256 : 512;
       pick_buffers(g, 8 * NP, pass == 0 ? 256 : 512);
