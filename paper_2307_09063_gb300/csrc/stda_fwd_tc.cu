@@ -58,13 +58,8 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
 }
 
 // acc = a * b + acc on a pair of FP32 lanes in one instruction (packed FP32
-// FMA of sm_100-class GPUs; each lane rounds exactly like a scalar FMA).
-__device__ __forceinline__ void ffma2(float2& acc, float2 a, float2 b) {
-  asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mov.b64 rc, {%0, %1};\n\tfma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
-      : "+f"(acc.x), "+f"(acc.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-}
+// FMA of sm_100-class GPUs; each lane rounds like a scalar FMA).
+__device__ __forceinline__ void ffma2(float2& acc, float2 a, float2 b) { acc = __ffma2_rn(a, b, acc); }
 
 // A 16-byte pixel of a staged plane: 8 bf16 channels, or 16 E4M3 channels.
 template <bool F8>
@@ -170,14 +165,66 @@ __device__ __forceinline__ void batched(int n, L load, F use) {
   }
 }
 
-__device__ __forceinline__ void warp_sum_to(float v, float* dst) {
+// Recursive halving over the lanes of a warp: at lane offset O a lane keeps
+// half of its N values (the upper half if lane & O) and adds the partner's
+// copy of that half; once one value is left the remaining offsets are plain
+// butterfly adds. `base` tracks the channel index of the lane's values.
+template <int N, int O>
+__device__ __forceinline__ void halve(float* v, int lane, int& base) {
+  if constexpr (O > 0) {
+    if constexpr (N > 1) {
+      constexpr int H = N / 2;
+      const bool up = (lane & O) != 0;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) *dst += v;
+      for (int j = 0; j < H; ++j) {
+        const float send = up ? v[j] : v[j + H], keep = up ? v[j + H] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += H;
+      halve<H, O / 2>(v, lane, base);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      halve<1, O / 2>(v, lane, base);
+    }
+  }
 }
 
-// Issues every MMA of one CTA (one thread). Accumulator (tile i, acc a) sits
-// at TMEM column (i * nacc + a) * NP; K-steps of accumulator a are
+// dst[c] += sum over the warp's lanes of v[c], c < N (v is overwritten):
+// N/2 + N/4 + ... shuffles instead of 5 N.
+template <int N>
+__device__ __forceinline__ void warp_sums_to(float* v, float* dst) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  halve<N, 16>(v, lane, base);
+  constexpr int R = N >= 32 ? N / 32 : 1, SAME = N >= 32 ? 1 : 32 / N;  // values per lane, lanes per total
+  if ((lane & (SAME - 1)) == 0)
+#pragma unroll
+    for (int j = 0; j < R; ++j) dst[base + j] += v[j];
+}
+
+// OR of `pred` over the 128 threads of warp group g (named barrier 1 + g,
+// g < 4); also orders the group's threads like a barrier.
+template <int ID>
+__device__ __forceinline__ uint32_t bar_red_or(uint32_t pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "n"(ID)
+      : "memory");
+  return r;
+}
+__device__ __forceinline__ bool group_or(bool pred, int g) {
+  switch (g) {
+    case 0: return bar_red_or<1>(pred) != 0;
+    case 1: return bar_red_or<2>(pred) != 0;
+    case 2: return bar_red_or<3>(pred) != 0;
+    default: return bar_red_or<4>(pred) != 0;
+  }
+}
+
+// Accumulator a of a tile sits at TMEM column a * NP; its K-steps are
 // ks[(a % nph) * nsteps ...] for the main branch (a < nph) and the same
 // table for the residual branch (a >= nph).
 // Descriptor table: one entry per (accumulator, K-step), the low words of
@@ -395,10 +442,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
-          const __nv_bfloat16* row = sin + (c * RI + y - yi0 + ky - 1) * CW + x + 7;
-          float v[6];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) v[q] = __bfloat162float(row[q]);
+          // columns x - 1 .. x + 4 sit at row[x + 7 .. x + 12]: one 4-, one
+          // 8- and one 4-byte load (rows are 8-byte aligned, x % 4 == 0)
+          const __nv_bfloat16* row = sin + (c * RI + y - yi0 + ky - 1) * CW + x;
+          const uint32_t l = *(const uint32_t*)(row + 6), r = *(const uint32_t*)(row + 12);
+          const uint2 m = *(const uint2*)(row + 8);
+          const float v[6] = {__uint_as_float(l & 0xFFFF0000u), __uint_as_float(m.x << 16),
+                              __uint_as_float(m.x & 0xFFFF0000u), __uint_as_float(m.y << 16),
+                              __uint_as_float(m.y & 0xFFFF0000u), __uint_as_float(r << 16)};
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
             const float4 wa = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8];
@@ -488,60 +539,73 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const int m_lo = WP + 1;
-  // 3. stage 2 on the tensor cores, 128-row tiles through nbuf TMEM buffers;
-  // 4. epilogue: warp group g drains buffer g (warps g*4 .. g*4+3 cover the
-  // 128 TMEM lanes)
+  // 3. stage 2 on the tensor cores, 128-row tiles; 4. epilogue. Warp group
+  // g owns TMEM buffer g and the tiles g, g + nbuf, ...: its first thread
+  // issues a tile's MMAs and commits them to the group's mbarrier, the four
+  // warps drain the accumulators (warp g*4 + q reads lanes 32q .. 32q + 31),
+  // then the group takes its next tile. Groups run unsynchronised, so one
+  // group's epilogue overlaps another group's MMAs.
   const int cpt = 2 * NP;  // TMEM columns per tile
-  for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
-    if (tid == 0)
-      for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
-        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.dtab, nsteps, 1, NP, (uint32_t)(128 * (t0 + k)), T,
-                       (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4);
-        commit(M.bar + k);
-      }
-    const int g = warp >> 2, i = t0 + g;
-    bool ok = true;
-    if (g < a.nbuf && i < a.ntile) {
-      ok = mbar_wait(M.bar + g, (phases >> g) & 1u);
-      fence_after_sync();
-      if (ok) {
-        const uint32_t col = (uint32_t)(g * cpt);
-        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-        int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
-        bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
-        __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
+  bool ok = true;
+  {
+    const int g = warp >> 2;
+    if (g < a.nbuf) {
+      uint32_t par = (phases >> g) & 1u;
+      const uint32_t col = (uint32_t)(g * cpt);
+      const bool issuer = (warp & 3) == 0 && lane == 0;
+      for (int i = g; i < a.ntile; i += a.nbuf) {
+        if (issuer) {
+          fence_after_sync();
+          issue_tile<F8>(tmem + col, M.dtab, nsteps, 1, NP, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
+                         (uint32_t)(L.wbytes / T) >> 4);
+          commit(M.bar + g);
+        }
+        __syncwarp();
+        ok = mbar_wait(M.bar + g, par);
+        par ^= 1u;
+        fence_after_sync();
+        if (ok) {
+          int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+          int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
+          bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
+          __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
 #pragma unroll
-        for (int c = 0; c < CO; c += 16) {
-          float mv[16], rv[16];
-          ld16(lane_addr(tmem, warp, col + c), mv);
-          ld16(lane_addr(tmem, warp, col + NP + c), rv);
-          ld_wait();
-          float o[16];
+          for (int c = 0; c < CO; c += 16) {
+            float mv[16], rv[16];
+            ld16(lane_addr(tmem, warp, col + c), mv);
+            ld16(lane_addr(tmem, warp, col + NP + c), rv);
+            ld_wait();
+            float o[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
-                               a.rb[c + j])
-                         : 0.f;
-          if (valid) {
-            *(uint4*)(dst + c) = f32_to_bf16x8(o);
-            *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
+            for (int j = 0; j < 16; ++j)
+              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
+                                 a.rb[c + j])
+                           : 0.f;
+            if (valid) {
+              *(uint4*)(dst + c) = f32_to_bf16x8(o);
+              *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
+            }
+            warp_sums_to<16>(o, &M.red[warp * CO + c]);
           }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) warp_sum_to(o[j], &M.red[warp * CO + c + j]);
+        }
+        // the group has read the buffer before its next tile overwrites it;
+        // on a timeout the issuer gives its MMAs a second bounded wait
+        fence_before_sync();
+        if (group_or(!ok, g)) {
+          if (issuer) mbar_wait(M.bar + g, par ^ 1u);
+          ok = false;
+          break;
         }
       }
     }
-    for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) phases ^= 1u << k;
-    fence_before_sync();
-    // CTA-wide agreement on the bounded waits; on a timeout the CTA records
-    // the error, lets its MMAs drain (bounded) and stops
-    failed = __syncthreads_or(!ok);
-    fence_after_sync();
   }
+  // every thread advances each buffer's phase by the tiles committed to it
+  for (int k = 0; k < a.nbuf && k < a.ntile; ++k) phases ^= (uint32_t)(((a.ntile - 1 - k) / a.nbuf + 1) & 1) << k;
+  fence_before_sync();
+  failed = __syncthreads_or(!ok);
+  fence_after_sync();
   if (failed) {
     if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
-    for (int k = 0; k < a.nbuf; ++k) mbar_wait(M.bar + k, ((phases >> k) & 1u) ^ 1u);
     break;
   }
   float* part = a.part + ((size_t)b * a.tiles_per_window + band) * CO;
@@ -676,59 +740,71 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
+  // stage 2 on the tensor cores and the epilogue, one warp group per TMEM
+  // buffer as in the encoder
   const int cpt = 8 * NP;  // TMEM columns per tile: 4 phases x (main, residual)
-  for (int t0 = 0; t0 < a.ntile && !failed; t0 += a.nbuf) {
-    if (tid == 0)
-      for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) {
-        issue_tile<F8>(tmem + (uint32_t)(k * cpt), M.dtab, nsteps, 4, NP, (uint32_t)(128 * (t0 + k)), T,
-                       (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4);
-        commit(M.bar + k);
-      }
-    const int g = warp >> 2, i = t0 + g;
-    bool ok = true;
-    if (g < a.nbuf && i < a.ntile) {
-      ok = mbar_wait(M.bar + g, (phases >> g) & 1u);
-      fence_after_sync();
-      if (ok) {
-        const uint32_t col = (uint32_t)(g * cpt);
-        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-        int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
-        bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
-        // channel sums over the four output phases in a fixed order, then one
-        // warp reduction per channel
+  bool ok = true;
+  {
+    const int g = warp >> 2;
+    if (g < a.nbuf) {
+      uint32_t par = (phases >> g) & 1u;
+      const uint32_t col = (uint32_t)(g * cpt);
+      const bool issuer = (warp & 3) == 0 && lane == 0;
+      for (int i = g; i < a.ntile; i += a.nbuf) {
+        if (issuer) {
+          fence_after_sync();
+          issue_tile<F8>(tmem + col, M.dtab, nsteps, 4, NP, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
+                         (uint32_t)(L.wbytes / T) >> 4);
+          commit(M.bar + g);
+        }
+        __syncwarp();
+        ok = mbar_wait(M.bar + g, par);
+        par ^= 1u;
+        fence_after_sync();
+        if (ok) {
+          int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+          int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
+          bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
+          // channel sums over the four output phases in a fixed order, then
+          // one warp reduction per 8 channels
 #pragma unroll 1
-        for (int cc = 0; cc < CO; cc += 8) {
-          float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int cc = 0; cc < CO; cc += 8) {
+            float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int ph = 0; ph < 4; ++ph) {
-            int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
-            __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
-            float mv[8], rv[8], o[8];
-            ld8(lane_addr(tmem, warp, col + ph * NP + cc), mv);
-            ld8(lane_addr(tmem, warp, col + (4 + ph) * NP + cc), rv);
-            ld_wait();
+            for (int ph = 0; ph < 4; ++ph) {
+              int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
+              __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
+              float mv[8], rv[8], o[8];
+              ld8(lane_addr(tmem, warp, col + ph * NP + cc), mv);
+              ld8(lane_addr(tmem, warp, col + (4 + ph) * NP + cc), rv);
+              ld_wait();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
-                                 a.b2[cc + j], a.rb[cc + j])
-                           : 0.f;
-              sum[j] += o[j];
+              for (int j = 0; j < 8; ++j) {
+                o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
+                                   a.b2[cc + j], a.rb[cc + j])
+                             : 0.f;
+                sum[j] += o[j];
+              }
+              if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
             }
-            if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
+            warp_sums_to<8>(sum, &M.red[warp * CO + cc]);
           }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) warp_sum_to(sum[j], &M.red[warp * CO + cc + j]);
+        }
+        fence_before_sync();
+        if (group_or(!ok, g)) {
+          if (issuer) mbar_wait(M.bar + g, par ^ 1u);
+          ok = false;
+          break;
         }
       }
     }
-    for (int k = 0; k < a.nbuf && t0 + k < a.ntile; ++k) phases ^= 1u << k;
-    fence_before_sync();
-    failed = __syncthreads_or(!ok);
-    fence_after_sync();
   }
+  for (int k = 0; k < a.nbuf && k < a.ntile; ++k) phases ^= (uint32_t)(((a.ntile - 1 - k) / a.nbuf + 1) & 1) << k;
+  fence_before_sync();
+  failed = __syncthreads_or(!ok);
+  fence_after_sync();
   if (failed) {
     if (tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
-    for (int k = 0; k < a.nbuf; ++k) mbar_wait(M.bar + k, ((phases >> k) & 1u) ^ 1u);
     break;
   }
   float* part = a.part + ((size_t)b * a.tiles_per_window + band) * CO;
@@ -803,6 +879,12 @@ int geo_policy() {
   return p;
 }
 
+// Plane stride skew in 16-byte pixels. The staging and stage-1 loops give
+// consecutive lanes the `touched` planes of one position, then the next
+// positions; with a plane stride of (8 / touched) mod 8 pixels, the eight
+// 16-byte accesses of each quarter-warp fall in distinct bank groups.
+int plane_skew(int touched) { return touched >= 8 ? 1 : 8 / touched; }
+
 Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
   const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
   const bool stem = b == 0;
@@ -815,7 +897,7 @@ Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
       int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8 + 1;  // plane stride 16 mod 128 bytes: no bank conflicts
+      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(2 * G);
       int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
       g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms).total;
       g.threads = pass == 0 ? 256 : 512;
@@ -838,7 +920,7 @@ Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
       int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8 + 1;  // plane stride 16 mod 128 bytes: no bank conflicts
+      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
       g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0, terms).total;
       g.threads = pass == 0 ? 256 : 512;
       pick_buffers(g, 8 * NP, pass == 0 ? 256 : 512);
