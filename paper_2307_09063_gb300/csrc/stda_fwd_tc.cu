@@ -282,6 +282,13 @@ __device__ __forceinline__ void issue_tile(uint32_t d_base, const uint2* tab, in
   }
 }
 
+// Decoder blocks with Cin <= 32 stack the four output phases along N: one
+// accumulator per branch of N = 4 Cout columns (column ph * Cout + n), one
+// K-step per (input offset, channel-group pair) with zero weights for the
+// phases that do not read that offset. Wider blocks keep one accumulator
+// per phase (N = Cout), whose stacked weights would not fit shared memory.
+__host__ __device__ constexpr bool dec_stacked(int ci) { return ci <= 32; }
+
 // Shared-memory carve-up, identical on host and device.
 struct Smem {
   int wbytes, planes_bytes, in_bytes;
@@ -623,10 +630,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
 template <int CI, bool SKIP, bool F8>
 __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   using OP = Op<F8>;
-  constexpr int CG = OP::CG, G = CI / CG, CO = CI / 2, NP = CO < 16 ? 16 : CO;
+  constexpr int CG = OP::CG, G = CI / CG, CO = CI / 2;
+  // accumulators per branch, N per MMA, TMEM column stride between phases
+  constexpr bool STACK = dec_stacked(CI);
+  constexpr int NPH = STACK ? 1 : 4, NM = STACK ? 4 * CO : (CO < 16 ? 16 : CO), PS = STACK ? CO : NM;
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int nsteps = a.nsteps, T = a.L.terms;  // K-steps per output phase
-  const Smem L = smem_layout(4 * nsteps, NP, G, a.PIXA, 0, T);
+  const int nsteps = a.nsteps, T = a.L.terms;  // K-steps per accumulator
+  const Smem L = smem_layout(NPH * nsteps, NM, G, a.PIXA, 0, T);
   const size_t lo_off = (size_t)G * a.PIXA * 16;
   Misc M(sm + L.off_misc, CI);
   unsigned char* x0 = sm + L.off_x0;
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
   copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
   const int m_lo = 2 * WP + 2;
-  fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, 4, NP, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
+  fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, NPH, NM, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
@@ -742,7 +752,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   fence_after_sync();
   // stage 2 on the tensor cores and the epilogue, one warp group per TMEM
   // buffer as in the encoder
-  const int cpt = 8 * NP;  // TMEM columns per tile: 4 phases x (main, residual)
+  const int cpt = 2 * NPH * NM;  // TMEM columns per tile: (main, residual) x 4 phases
   bool ok = true;
   {
     const int g = warp >> 2;
@@ -753,7 +763,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
       for (int i = g; i < a.ntile; i += a.nbuf) {
         if (issuer) {
           fence_after_sync();
-          issue_tile<F8>(tmem + col, M.dtab, nsteps, 4, NP, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
+          issue_tile<F8>(tmem + col, M.dtab, nsteps, NPH, NM, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
                          (uint32_t)(L.wbytes / T) >> 4);
           commit(M.bar + g);
         }
@@ -775,12 +785,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
               int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
               __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
               float mv[8], rv[8], o[8];
-              ld8(lane_addr(tmem, warp, col + ph * NP + cc), mv);
-              ld8(lane_addr(tmem, warp, col + (4 + ph) * NP + cc), rv);
+              const int mc = ph * PS + cc;  // main column; residual 4 PS further
+              ld8(lane_addr(tmem, warp, col + mc), mv);
+              ld8(lane_addr(tmem, warp, col + 4 * PS + mc), rv);
               ld_wait();
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[cc + j] : 1.f, F8 ? a.L.swr[cc + j] : 1.f,
+                o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[mc + j] : 1.f, F8 ? a.L.swr[mc + j] : 1.f,
                                    a.b2[cc + j], a.rb[cc + j])
                              : 0.f;
                 sum[j] += o[j];
@@ -831,14 +842,14 @@ int cdiv(int a, int b) { return (a + b - 1) / b; }
 // K-step instead.
 int steps_per_acc(int b, bool f8) {
   const int G = kBlkCin[b] / (f8 ? 16 : 8);
-  if (kBlkEnc[b]) return G == 1 ? 5 : 9 * G / 2;
+  if (kBlkEnc[b] || dec_stacked(kBlkCin[b])) return G == 1 ? 5 : 9 * G / 2;
   return G == 1 ? 2 : 4 * G / 2;
 }
 
-// Band geometry of one level: the largest band (8, 4, 2 or 1 rows) whose
-// accumulators fit the TMEM columns and whose planes fit shared memory.
-// Two passes: first a band that lets two CTAs share an SM (shared memory
-// <= half, TMEM <= 256 columns), then any band that fits.
+// Band geometry of one level: the largest band (16, 8, 4, 2 or 1 rows)
+// whose accumulators fit the TMEM columns and whose planes and weights fit
+// shared memory; at equal band, two CTAs of 256 threads per SM (shared
+// memory <= half, TMEM <= 256 columns) before one CTA of 512 threads.
 struct Geo {
   int band, ntile, WP, PIXA, smem, threads, nbuf;
   uint32_t cols;
@@ -868,8 +879,9 @@ int band_cap(int b) {
   return caps[b];
 }
 
-// Geometry policy: 0 = prefer two CTAs per SM, then the largest band;
-// 1 = prefer the largest band (either CTA shape). STDA_TC_POLICY overrides.
+// Geometry policy: 0 = the largest band first (default; the faster one
+// measured on 256 windows of 3 x 256 x 128 in bf16 and 1024 windows of
+// 3 x 512 x 256 in FP8); 1 = two CTAs per SM first, then the largest band. STDA_TC_POLICY overrides.
 int geo_policy() {
   static int p = -1;
   if (p < 0) {
@@ -890,7 +902,7 @@ Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
   const bool stem = b == 0;
   Geo g{};
   for (int it = 0; it < 10; ++it) {
-      const int pass = geo_policy() ? it % 2 : it / 5, TY = 16 >> (geo_policy() ? it / 2 : it % 5);
+      const int pass = geo_policy() ? it / 5 : it % 2, TY = 16 >> (geo_policy() ? it % 5 : it / 2);
       if (band_cap(b) && TY > band_cap(b)) continue;
       g.band = TY;
       g.WP = wo + 2;
@@ -911,19 +923,21 @@ Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
 Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
   const int CI = kBlkCin[b], CO = CI / 2, G = CI / (f8 ? 16 : 8), NP = CO < 16 ? 16 : CO,
             nsteps = steps_per_acc(b, f8);
+  const bool stack = dec_stacked(CI);
+  const int nph = stack ? 1 : 4, NM = stack ? 4 * CO : NP;  // accumulators per branch, N per MMA
   Geo g{};
   for (int it = 0; it < 10; ++it) {
-      const int pass = geo_policy() ? it % 2 : it / 5, TA = 16 >> (geo_policy() ? it / 2 : it % 5);
+      const int pass = geo_policy() ? it / 5 : it % 2, TA = 16 >> (geo_policy() ? it % 5 : it / 2);
       if (band_cap(b) && TA > band_cap(b)) continue;
       g.band = TA;
       g.WP = w + 4;
       int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
       g.ntile = cdiv(count, 128);
-      g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 1);
+      g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 2);
       g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-      g.smem = smem_layout(4 * nsteps, NP, G, g.PIXA, 0, terms).total;
+      g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms).total;
       g.threads = pass == 0 ? 256 : 512;
-      pick_buffers(g, 8 * NP, pass == 0 ? 256 : 512);
+      pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512);
       if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
     }
   g.band = 0;
@@ -977,10 +991,11 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
   };
   for (int b = 0; b < kNumBlocks; ++b) {
     const int ci = kBlkCin[b], co = kBlkCout[b], CG = f8[b] ? 16 : 8, G = ci / CG;
-    const bool enc = kBlkEnc[b];
-    const int NP = enc ? co : (co < 16 ? 16 : co);
+    const bool enc = kBlkEnc[b], stack = !enc && dec_stacked(ci);
+    // N per MMA: Cout (encoder), 4 Cout (stacked decoder), Cout padded to 16
+    const int NP = enc ? co : stack ? 4 * co : (co < 16 ? 16 : co);
     struct Half {
-      int tap, g;  // tap < 0: zero half
+      int tap, g;  // tap < 0: zero half; stacked decoder: input offset index
     };
     std::vector<KStep> ks;
     std::vector<std::pair<Half, Half>> halves;
@@ -1008,6 +1023,25 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
             add(t, 2 * kg, plane(t, 2 * kg), tap_shift(t / 3), tap_shift(t % 3), t, 2 * kg + 1, plane(t, 2 * kg + 1),
                 tap_shift(t / 3), tap_shift(t % 3));
       }
+    } else if (stack) {
+      // input offset o = (dy + 1) * 3 + (dx + 1), dy, dx in {-1, 0, 1}
+      auto odr = [](int o) { return o / 3 - 1; };
+      auto odc = [](int o) { return o % 3 - 1; };
+      if (G == 1) {
+        // pairs of offsets in the one plane, second half at a larger address
+        const int pairs[5][2] = {{0, 1}, {3, 4}, {6, 7}, {2, 5}, {8, -1}};
+        for (auto& pr : pairs) {
+          int o0 = pr[0], o1 = pr[1];
+          if (o1 >= 0)
+            add(o0, 0, 0, odr(o0), odc(o0), o1, 0, 0, odr(o1), odc(o1));
+          else
+            add(o0, 0, 0, odr(o0), odc(o0), -1, 0, 0, odr(o0), odc(o0) + 1);
+        }
+      } else {
+        for (int o = 0; o < 9; ++o)
+          for (int kg = 0; kg < G / 2; ++kg)
+            add(o, 2 * kg, 2 * kg, odr(o), odc(o), o, 2 * kg + 1, 2 * kg + 1, odr(o), odc(o));
+      }
     } else {
       for (int ph = 0; ph < 4; ++ph) {
         const int py = ph >> 1, px = ph & 1;
@@ -1026,7 +1060,16 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
     for (int br = 0; br < 2; ++br) {
       const float* src = folded + (br == 0 ? off.w2[b] : off.rw[b]);
       auto wt = [&](const Half& h, int n, int c) {
-        return (h.tap >= 0 && n < co) ? src[((size_t)h.tap * ci + h.g * CG + c) * co + n] : 0.f;
+        if (h.tap < 0) return 0.f;
+        if (stack) {
+          // row n = phase * Cout + channel; phase (py, px) reads input
+          // offsets dy in {py - 1, py}, dx in {px - 1, px} through sub-tap
+          // (dy - py + 1, dx - px + 1)
+          const int ph = n / co, oc = n % co, sy = h.tap / 3 - 1 - (ph >> 1) + 1, sx = h.tap % 3 - 1 - (ph & 1) + 1;
+          if (sy < 0 || sy > 1 || sx < 0 || sx > 1) return 0.f;
+          return src[((size_t)(ph * 4 + sy * 2 + sx) * ci + h.g * CG + c) * co + oc];
+        }
+        return n < co ? src[((size_t)h.tap * ci + h.g * CG + c) * co + n] : 0.f;
       };
       // per output channel scale (E4M3): max |w| / 448
       std::vector<float> sc(NP, 1.f);
@@ -1067,8 +1110,10 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
                 }
               }
           }
+      // decoders read the scale of TMEM column ph * PS + n: the unstacked
+      // layout repeats its per-channel scales for the four phases
       sc_start[b][br] = scales.size();
-      scales.insert(scales.end(), sc.begin(), sc.end());
+      for (int rep = 0; rep < (!enc && !stack ? 4 : 1); ++rep) scales.insert(scales.end(), sc.begin(), sc.end());
     }
     ks_start[b] = ks_all.size();
     ks_all.insert(ks_all.end(), ks.begin(), ks.end());
