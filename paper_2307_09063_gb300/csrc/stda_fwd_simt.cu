@@ -541,66 +541,78 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
 }
 
 // Output module for bf16 maps: the ECA weights of decoder block 3 are folded
-// into the conv weights of each window (the conv is linear in its input), the
-// 72 weights live in registers, and each thread computes four horizontally
-// adjacent pixels from the 3 x 6 neighbourhood read straight from global
-// memory (16 bytes = 8 channels per pixel; neighbouring threads share rows
-// through L1).
-__global__ void __launch_bounds__(kThreads, 2) k_out_bf16(OutArgs<__nv_bfloat16> a) {
+// into the conv weights of each window (the conv is linear in its input) and
+// kept in registers as channel pairs. A CTA takes one window and a band of
+// kOutRows output rows; each thread owns one column and walks down the input
+// rows, loading the three pixels (x - 1, x, x + 1; 16 bytes = 8 channels
+// each) of a row once, one row ahead of use. Input row r feeds the
+// accumulators of output rows r + 1, r and r - 1 (kernel rows 0, 1, 2);
+// after row r, output row r - 1 is complete.
+constexpr int kOutRows = 32;
+
+__device__ __forceinline__ void out_row(const uint4 (&u)[3], const float2* wr, int dy, float2& acc) {
+#pragma unroll
+  for (int dx = 0; dx < 3; ++dx) {
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(&u[dx]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = make_float2(__uint_as_float(q[k] << 16), __uint_as_float(q[k] & 0xFFFF0000u));
+      acc = __ffma2_rn(f, wr[(dy * 3 + dx) * 4 + k], acc);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a) {
   __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
   __shared__ float s_w[72];
-  const int b = blockIdx.y, H = a.H, W = a.W, W4 = W / 4;
+  const int b = blockIdx.y, H = a.H, W = a.W;
+  const int y0 = blockIdx.x * kOutRows, y1 = min(H, y0 + kOutRows);
   eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_tmp, s_g, s_s);
   for (int i = threadIdx.x; i < 72; i += blockDim.x) s_w[i] = a.w.out_w[i] * s_s[i & 7];
   __syncthreads();
-  float wr[72];
+  float2 wr[36];
 #pragma unroll
-  for (int i = 0; i < 72; ++i) wr[i] = s_w[i];
+  for (int i = 0; i < 36; ++i) wr[i] = make_float2(s_w[2 * i], s_w[2 * i + 1]);
   const float bias = a.w.out_b[0];
   const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
-  for (int strip = blockIdx.x * blockDim.x + threadIdx.x; strip < H * W4; strip += gridDim.x * blockDim.x) {
-    const int y = strip / W4, x0 = (strip % W4) * 4;
-    float z[4] = {bias, bias, bias, bias};
+  __nv_bfloat16* out = a.out + (size_t)b * H * W;
+  auto load_row = [&](int r, int x, uint4(&u)[3]) {
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      const int yy = y + dy - 1;
-      if (yy < 0 || yy >= H) continue;
-#pragma unroll
-      for (int cx = 0; cx < 6; ++cx) {
-        const int xx = x0 + cx - 1;
-        if (xx < 0 || xx >= W) continue;
-        uint4 u = *(const uint4*)(A + ((size_t)yy * W + xx) * 8);
-        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
-        float f[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float2 t = __bfloat1622float2(hv[k]);
-          f[2 * k] = t.x;
-          f[2 * k + 1] = t.y;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int kx = cx - j;
-          if (kx < 0 || kx > 2) continue;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) z[j] += wr[(dy * 3 + kx) * 8 + c] * f[c];
-        }
-      }
+    for (int dx = 0; dx < 3; ++dx) {
+      const int xx = x + dx - 1;
+      u[dx] = (r >= 0 && r < H && xx >= 0 && xx < W) ? *(const uint4*)(A + ((size_t)r * W + xx) * 8)
+                                                      : make_uint4(0, 0, 0, 0);
     }
-    __nv_bfloat16 o[4];
+  };
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    // acc[0], acc[1], acc[2]: output rows r - 1, r, r + 1 while reading row r
+    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    uint4 cur[3], nxt[3];
+    load_row(y0 - 1, x, cur);
+    for (int r = y0 - 1; r <= y1; ++r) {
+      if (r < y1) load_row(r + 1, x, nxt);
+      out_row(cur, wr, 2, acc[0]);
+      out_row(cur, wr, 1, acc[1]);
+      out_row(cur, wr, 0, acc[2]);
+      if (r - 1 >= y0) {
+        const float z = acc[0].x + acc[0].y + bias;
+        out[(size_t)(r - 1) * W + x] = __float2bfloat16_rn(1.f / (1.f + expf(-z)));
+      }
+      acc[0] = acc[1];
+      acc[1] = acc[2];
+      acc[2] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) o[j] = __float2bfloat16_rn(1.f / (1.f + expf(-z[j])));
-    *(uint2*)(a.out + ((size_t)b * H + y) * W + x0) = *(const uint2*)o;
+      for (int dx = 0; dx < 3; ++dx) cur[dx] = nxt[dx];
+    }
   }
 }
 
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
                             __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook) {
   OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
-  const int strips = H * (W / 4);
+  const int threads = std::min(kThreads, (W + 31) / 32 * 32);
   hook->begin(K_OUT, st);
-  // about eight strips per thread: the per-CTA ECA reduction is amortised
-  k_out_bf16<<<dim3(std::max(1, cdiv(strips, kThreads * 8)), B), kThreads, 0, st>>>(a);
+  k_out_bf16<<<dim3(cdiv(H, kOutRows), B), threads, 0, st>>>(a);
   hook->end(st);
   return cudaGetLastError();
 }
