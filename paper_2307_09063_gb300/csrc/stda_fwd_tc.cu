@@ -313,8 +313,8 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
 // Misc area: [0, 1024) descriptor table (up to 128 entries), [1024, 1536)
 // ECA g / s (input), [1536, 2048) ECA s (skip), [2048, 4608) stage-1 weights
 // + bias, [4608, 5632) stem weights + bias, [5632, 9728) per-warp channel
-// sums (up to 16 warps), [9728, 9760) mbarriers (one per TMEM tile buffer),
-// [9760] TMEM slot.
+// sums (up to 16 warps), [9728, 9792) mbarriers (group g, slot s at 2 g + s),
+// [9792] TMEM slot.
 struct Misc {
   uint2* dtab;
   float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red;
@@ -331,7 +331,7 @@ struct Misc {
     stb = stw + 216;
     red = (float*)(p + 5632);
     bar = (uint64_t*)(p + 9728);
-    tslot = (uint32_t*)(p + 9760);
+    tslot = (uint32_t*)(p + 9792);
   }
 };
 
@@ -363,6 +363,64 @@ __device__ __forceinline__ float epi(float m, float r, float sm, float sr, float
   return fmaxf(m * sm + b2, 0.f) + r * sr + rb;
 }
 
+// The tiles of one item. Warp group g (< a.nbuf) owns the TMEM slots
+// (g * nslot + s) * cpt, s < nslot, their mbarriers 2 g + s and the tiles
+// g, g + nbuf, ...: its first thread issues a tile's MMAs and commits them,
+// the four warps drain the accumulators (warp 4 g + q reads TMEM lanes
+// 32 q .. 32 q + 31) through drain(tile, column). With two slots the next
+// tile is queued before the drain, so the tensor core runs it meanwhile;
+// groups run unsynchronised, so one group's drain also overlaps other
+// groups' MMAs. Bounded waits; a timeout is agreed per group (the issuer
+// gives its queued MMAs a second bounded wait) and returned as false.
+// `phases` holds bit 2 g + s = parity of that barrier's next completion.
+template <bool F8, typename Drain>
+__device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32_t tmem, uint32_t& phases,
+                                          int cpt, int nsteps, int nph, int NM, int T, uint32_t a_lo,
+                                          uint32_t b_lo, Drain drain) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = warp >> 2, ng = a.nbuf, ns = a.nslot;
+  bool ok = true;
+  if (g < ng) {
+    const bool issuer = (warp & 3) == 0 && lane == 0;
+    uint32_t par = (phases >> (2 * g)) & 3u;
+    auto issue = [&](int tile, int s) {
+      fence_after_sync();
+      issue_tile<F8>(tmem + (uint32_t)((g * ns + s) * cpt), M.dtab, nsteps, nph, NM, (uint32_t)(128 * tile), T,
+                     a_lo, b_lo);
+      commit(M.bar + 2 * g + s);
+    };
+    if (issuer && g < a.ntile) issue(g, 0);
+    int k = 0;
+    for (int i = g; i < a.ntile; i += ng, ++k) {
+      const int s = ns == 2 ? (k & 1) : 0;
+      const bool next = i + ng < a.ntile;
+      if (ns == 2 && issuer && next) issue(i + ng, s ^ 1);
+      __syncwarp();
+      ok = mbar_wait(M.bar + 2 * g + s, (par >> s) & 1u);
+      par ^= 1u << s;
+      fence_after_sync();
+      if (ok) drain(i, (uint32_t)((g * ns + s) * cpt));
+      // the group has read the slot before a later tile overwrites it
+      fence_before_sync();
+      if (group_or(!ok, g)) {
+        if (issuer) {
+          mbar_wait(M.bar + 2 * g + s, ((par >> s) & 1u) ^ 1u);
+          if (ns == 2 && next) mbar_wait(M.bar + 2 * g + (s ^ 1), (par >> (s ^ 1)) & 1u);
+        }
+        ok = false;
+        break;
+      }
+      if (ns == 1 && issuer && next) issue(i + ng, 0);
+    }
+  }
+  // every thread advances every barrier's phase by the commits of this item
+  for (int gg = 0; gg < ng; ++gg) {
+    const int n = gg < a.ntile ? (a.ntile - 1 - gg) / ng + 1 : 0;
+    const int n0 = ns == 2 ? (n + 1) / 2 : n, n1 = ns == 2 ? n / 2 : 0;
+    phases ^= ((uint32_t)(n0 & 1) << (2 * gg)) | ((uint32_t)(n1 & 1) << (2 * gg + 1));
+  }
+  return ok;
+}
+
 // ---------------------------------------------------------------- encoder
 template <int CI, bool STEM, bool F8>
 __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
@@ -386,7 +444,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
 
   // once per CTA: weights, tables, barrier, tensor memory
   if (tid == 0) {
-    for (int k = 0; k < a.nbuf; ++k) mbar_init(M.bar + k, 1);
+    for (int k = 0; k < 2 * a.nbuf; ++k) mbar_init(M.bar + k, 1);
     mbar_fence_init();
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
@@ -405,7 +463,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
-  uint32_t phases = 0;  // bit k: parity of buffer k's next completion
+  uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
   const int items = a.tiles_per_window * a.nwin;
   bool failed = false;
 
@@ -546,68 +604,34 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  // 3. stage 2 on the tensor cores, 128-row tiles; 4. epilogue. Warp group
-  // g owns TMEM buffer g and the tiles g, g + nbuf, ...: its first thread
-  // issues a tile's MMAs and commits them to the group's mbarrier, the four
-  // warps drain the accumulators (warp g*4 + q reads lanes 32q .. 32q + 31),
-  // then the group takes its next tile. Groups run unsynchronised, so one
-  // group's epilogue overlaps another group's MMAs.
+  // 3. stage 2 on the tensor cores, 128-row tiles; 4. epilogue
   const int cpt = 2 * NP;  // TMEM columns per tile
-  bool ok = true;
-  {
-    const int g = warp >> 2;
-    if (g < a.nbuf) {
-      uint32_t par = (phases >> g) & 1u;
-      const uint32_t col = (uint32_t)(g * cpt);
-      const bool issuer = (warp & 3) == 0 && lane == 0;
-      for (int i = g; i < a.ntile; i += a.nbuf) {
-        if (issuer) {
-          fence_after_sync();
-          issue_tile<F8>(tmem + col, M.dtab, nsteps, 1, NP, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
-                         (uint32_t)(L.wbytes / T) >> 4);
-          commit(M.bar + g);
-        }
-        __syncwarp();
-        ok = mbar_wait(M.bar + g, par);
-        par ^= 1u;
-        fence_after_sync();
-        if (ok) {
-          int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-          int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
-          bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
-          __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
+  const bool ok = run_tiles<F8>(
+      a, M, tmem, phases, cpt, nsteps, 1, NP, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
+      [&](int i, uint32_t col) {
+        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+        int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
+        bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
+        __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
 #pragma unroll
-          for (int c = 0; c < CO; c += 16) {
-            float mv[16], rv[16];
-            ld16(lane_addr(tmem, warp, col + c), mv);
-            ld16(lane_addr(tmem, warp, col + NP + c), rv);
-            ld_wait();
-            float o[16];
+        for (int c = 0; c < CO; c += 16) {
+          float mv[16], rv[16];
+          ld16(lane_addr(tmem, warp, col + c), mv);
+          ld16(lane_addr(tmem, warp, col + NP + c), rv);
+          ld_wait();
+          float o[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
-                                 a.rb[c + j])
-                           : 0.f;
-            if (valid) {
-              *(uint4*)(dst + c) = f32_to_bf16x8(o);
-              *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
-            }
-            warp_sums_to<16>(o, &M.red[warp * CO + c]);
+          for (int j = 0; j < 16; ++j)
+            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
+                               a.rb[c + j])
+                         : 0.f;
+          if (valid) {
+            *(uint4*)(dst + c) = f32_to_bf16x8(o);
+            *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
           }
+          warp_sums_to<16>(o, &M.red[warp * CO + c]);
         }
-        // the group has read the buffer before its next tile overwrites it;
-        // on a timeout the issuer gives its MMAs a second bounded wait
-        fence_before_sync();
-        if (group_or(!ok, g)) {
-          if (issuer) mbar_wait(M.bar + g, par ^ 1u);
-          ok = false;
-          break;
-        }
-      }
-    }
-  }
-  // every thread advances each buffer's phase by the tiles committed to it
-  for (int k = 0; k < a.nbuf && k < a.ntile; ++k) phases ^= (uint32_t)(((a.ntile - 1 - k) / a.nbuf + 1) & 1) << k;
+      });
   fence_before_sync();
   failed = __syncthreads_or(!ok);
   fence_after_sync();
@@ -648,7 +672,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   auto px = [&](unsigned char* base, int g, int p) { return (uint4*)(base + ((size_t)g * PIXA + p) * 16); };
 
   if (tid == 0) {
-    for (int k = 0; k < a.nbuf; ++k) mbar_init(M.bar + k, 1);
+    for (int k = 0; k < 2 * a.nbuf; ++k) mbar_init(M.bar + k, 1);
     mbar_fence_init();
   }
   copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
@@ -663,7 +687,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
-  uint32_t phases = 0;  // bit k: parity of buffer k's next completion
+  uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
   const int items = a.tiles_per_window * a.nwin;
   bool failed = false;
   const float inv_n = 1.f / (float)(h * w);
@@ -750,67 +774,40 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  // stage 2 on the tensor cores and the epilogue, one warp group per TMEM
-  // buffer as in the encoder
+  // stage 2 on the tensor cores and the epilogue, as in the encoder
   const int cpt = 2 * NPH * NM;  // TMEM columns per tile: (main, residual) x 4 phases
-  bool ok = true;
-  {
-    const int g = warp >> 2;
-    if (g < a.nbuf) {
-      uint32_t par = (phases >> g) & 1u;
-      const uint32_t col = (uint32_t)(g * cpt);
-      const bool issuer = (warp & 3) == 0 && lane == 0;
-      for (int i = g; i < a.ntile; i += a.nbuf) {
-        if (issuer) {
-          fence_after_sync();
-          issue_tile<F8>(tmem + col, M.dtab, nsteps, NPH, NM, (uint32_t)(128 * i), T, (uint32_t)(lo_off >> 4),
-                         (uint32_t)(L.wbytes / T) >> 4);
-          commit(M.bar + g);
-        }
-        __syncwarp();
-        ok = mbar_wait(M.bar + g, par);
-        par ^= 1u;
-        fence_after_sync();
-        if (ok) {
-          int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
-          int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
-          bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
-          // channel sums over the four output phases in a fixed order, then
-          // one warp reduction per 8 channels
+  const bool ok = run_tiles<F8>(
+      a, M, tmem, phases, cpt, nsteps, NPH, NM, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
+      [&](int i, uint32_t col) {
+        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+        int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
+        bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
+        // channel sums over the four output phases in a fixed order, then
+        // one warp reduction per 8 channels
 #pragma unroll 1
-          for (int cc = 0; cc < CO; cc += 8) {
-            float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int cc = 0; cc < CO; cc += 8) {
+          float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int ph = 0; ph < 4; ++ph) {
-              int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
-              __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
-              float mv[8], rv[8], o[8];
-              const int mc = ph * PS + cc;  // main column; residual 4 PS further
-              ld8(lane_addr(tmem, warp, col + mc), mv);
-              ld8(lane_addr(tmem, warp, col + 4 * PS + mc), rv);
-              ld_wait();
+          for (int ph = 0; ph < 4; ++ph) {
+            int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
+            __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
+            float mv[8], rv[8], o[8];
+            const int mc = ph * PS + cc;  // main column; residual 4 PS further
+            ld8(lane_addr(tmem, warp, col + mc), mv);
+            ld8(lane_addr(tmem, warp, col + 4 * PS + mc), rv);
+            ld_wait();
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[mc + j] : 1.f, F8 ? a.L.swr[mc + j] : 1.f,
-                                   a.b2[cc + j], a.rb[cc + j])
-                             : 0.f;
-                sum[j] += o[j];
-              }
-              if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
+            for (int j = 0; j < 8; ++j) {
+              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[mc + j] : 1.f, F8 ? a.L.swr[mc + j] : 1.f,
+                                 a.b2[cc + j], a.rb[cc + j])
+                           : 0.f;
+              sum[j] += o[j];
             }
-            warp_sums_to<8>(sum, &M.red[warp * CO + cc]);
+            if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
           }
+          warp_sums_to<8>(sum, &M.red[warp * CO + cc]);
         }
-        fence_before_sync();
-        if (group_or(!ok, g)) {
-          if (issuer) mbar_wait(M.bar + g, par ^ 1u);
-          ok = false;
-          break;
-        }
-      }
-    }
-  }
-  for (int k = 0; k < a.nbuf && k < a.ntile; ++k) phases ^= (uint32_t)(((a.ntile - 1 - k) / a.nbuf + 1) & 1) << k;
+      });
   fence_before_sync();
   failed = __syncthreads_or(!ok);
   fence_after_sync();
@@ -851,20 +848,33 @@ int steps_per_acc(int b, bool f8) {
 // shared memory; at equal band, two CTAs of 256 threads per SM (shared
 // memory <= half, TMEM <= 256 columns) before one CTA of 512 threads.
 struct Geo {
-  int band, ntile, WP, PIXA, smem, threads, nbuf;
+  int band, ntile, WP, PIXA, smem, threads, nbuf, nslot;
   uint32_t cols;
 };
 
-// TMEM tile buffers: as many as warp groups, within the column budget.
+// Tuning override: STDA_TC_SLOTS=1 keeps one TMEM slot per warp group.
+int max_slots() {
+  static int m = -1;
+  if (m < 0) {
+    const char* e = getenv("STDA_TC_SLOTS");
+    m = (e && atoi(e) == 1) ? 1 : 2;
+  }
+  return m;
+}
+
+// Warp groups running tiles: as many as fit the TMEM column budget; then a
+// second slot per group if every group can have one.
 void pick_buffers(Geo& g, int cpt, int budget) {
   const int groups = g.threads / 128;
   g.nbuf = 0;
+  g.nslot = 1;
   for (int k = groups; k >= 1; --k)
     if ((int)pow2_cols(k * cpt) <= budget) {
       g.nbuf = k;
       break;
     }
-  g.cols = pow2_cols(std::max(g.nbuf, 1) * cpt);
+  if (max_slots() == 2 && g.nbuf == groups && (int)pow2_cols(2 * groups * cpt) <= budget) g.nslot = 2;
+  g.cols = pow2_cols(std::max(g.nbuf, 1) * g.nslot * cpt);
 }
 
 // Tuning override: STDA_TC_BANDS="e1,e2,e3,d1,d2,d3" caps each level's band
@@ -1180,6 +1190,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.PIXA = g.PIXA;
     a.tmem_cols = g.cols;
     a.nbuf = g.nbuf;
+    a.nslot = g.nslot;
     a.stem_w = w.stem_w;
     a.stem_b = w.stem_b;
     a.dw = w.blk[l].dw;

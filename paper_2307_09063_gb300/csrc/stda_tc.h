@@ -52,7 +52,8 @@ struct TcArgs {
   int WP, PIXA;   // plane pitch and pixels per plane
   int tiles_per_window;
   int nwin;  // windows in the batch (items = windows x bands)
-  int nbuf;  // TMEM tile buffers (1 .. warp groups)
+  int nbuf;   // warp groups that run tiles (1 .. 4), one MMA issuer each
+  int nslot;  // TMEM accumulator slots per group (2: next tile queued before the drain)
   int nsteps;
   uint32_t tmem_cols;
   const float *stem_w, *stem_b, *dw, *dwb, *b2, *rb;
