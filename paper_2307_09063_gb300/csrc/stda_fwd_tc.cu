@@ -289,13 +289,55 @@ __device__ __forceinline__ void issue_tile(uint32_t d_base, const uint2* tab, in
 // per phase (N = Cout), whose stacked weights would not fit shared memory.
 __host__ __device__ constexpr bool dec_stacked(int ci) { return ci <= 32; }
 
+// Per-kernel scratch ("misc") area, identical on host and device: mbarriers
+// (group g, slot s at 2 g + s) and the TMEM address slot first, then the MMA
+// descriptor table (two accumulators x phases x K-steps), ECA g / s of the
+// input (2 Cin) and of the skip (Cin), stage-1 weights and bias (10 Cin),
+// stem weights and bias (224, stem block only), per-warp channel sums (up to
+// 16 warps x Cout, also the ECA reduction scratch of up to 512 threads),
+// and the epilogue constants: BN shift and residual bias (Cout each) and the
+// E4M3 weight scales of the two branches (one per TMEM column of a branch).
+struct MiscLayout {
+  int bar, tslot, dtab, g, ss, dw, stem, red, b2, rb, sm, sr, total;
+};
+__host__ __device__ constexpr int k_steps_per_acc(int CI, bool enc, bool f8) {
+  const int G = CI / (f8 ? 16 : 8);
+  return (enc || dec_stacked(CI)) ? (G == 1 ? 5 : 9 * G / 2) : (G == 1 ? 2 : 2 * G);
+}
+__host__ __device__ constexpr int misc_take(int& off, int bytes) {
+  const int o = off;
+  off += (bytes + 15) / 16 * 16;
+  return o;
+}
+__host__ __device__ constexpr MiscLayout misc_layout(int CI, bool enc, bool f8) {
+  const int CO = enc ? 2 * CI : CI / 2, NPH = (enc || dec_stacked(CI)) ? 1 : 4;
+  const int PS = enc ? CO : dec_stacked(CI) ? CO : (CO < 16 ? 16 : CO), NCOL = enc ? CO : 4 * PS;
+  const int red = 16 * CO > 512 ? 16 * CO : 512;
+  int off = 0;
+  MiscLayout m{};
+  m.bar = misc_take(off, 64);
+  m.tslot = misc_take(off, 16);
+  m.dtab = misc_take(off, 8 * 2 * NPH * k_steps_per_acc(CI, enc, f8));
+  m.g = misc_take(off, 4 * 2 * CI);
+  m.ss = misc_take(off, 4 * CI);
+  m.dw = misc_take(off, 4 * 10 * CI);
+  m.stem = misc_take(off, enc && CI == 8 ? 4 * 224 : 0);
+  m.red = misc_take(off, 4 * red);
+  m.b2 = misc_take(off, 4 * CO);
+  m.rb = misc_take(off, 4 * CO);
+  m.sm = misc_take(off, 4 * NCOL);
+  m.sr = misc_take(off, 4 * NCOL);
+  m.total = (off + 127) / 128 * 128;
+  return m;
+}
+
 // Shared-memory carve-up, identical on host and device.
 struct Smem {
   int wbytes, planes_bytes, in_bytes;
   int off_wm, off_wr, off_x0, off_x1, off_in, off_misc, total;
 };
 __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplanes, int PIXA, int in_bytes,
-                                            int terms = 1) {
+                                            int terms, int misc_bytes) {
   Smem s;
   s.wbytes = terms * nsteps_total * 2 * NP * 16;
   s.planes_bytes = (terms * nplanes * PIXA * 16 + 127) / 128 * 128;
@@ -306,32 +348,32 @@ __host__ __device__ inline Smem smem_layout(int nsteps_total, int NP, int nplane
   s.off_x1 = s.off_x0 + s.planes_bytes;
   s.off_in = s.off_x1 + s.planes_bytes;
   s.off_misc = s.off_in + s.in_bytes;
-  s.total = s.off_misc + kTcMiscBytes;
+  s.total = s.off_misc + misc_bytes;
   return s;
 }
 
-// Misc area: [0, 1024) descriptor table (up to 128 entries), [1024, 1536)
-// ECA g / s (input), [1536, 2048) ECA s (skip), [2048, 4608) stage-1 weights
-// + bias, [4608, 5632) stem weights + bias, [5632, 9728) per-warp channel
-// sums (up to 16 warps), [9728, 9792) mbarriers (group g, slot s at 2 g + s),
-// [9792] TMEM slot.
+// Pointers into the misc area (layout above).
 struct Misc {
   uint2* dtab;
-  float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red;
+  float *g, *sa, *ss, *dw, *dwb, *stw, *stb, *red, *b2, *rb, *sm, *sr;
   uint64_t* bar;
   uint32_t* tslot;
-  __device__ Misc(unsigned char* p, int CI) {
-    dtab = (uint2*)p;
-    g = (float*)(p + 1024);
-    sa = g + 64;
-    ss = (float*)(p + 1536);
-    dw = (float*)(p + 2048);
+  __device__ Misc(unsigned char* p, const MiscLayout& l, int CI) {
+    bar = (uint64_t*)(p + l.bar);
+    tslot = (uint32_t*)(p + l.tslot);
+    dtab = (uint2*)(p + l.dtab);
+    g = (float*)(p + l.g);
+    sa = g + CI;
+    ss = (float*)(p + l.ss);
+    dw = (float*)(p + l.dw);
     dwb = dw + 9 * CI;
-    stw = (float*)(p + 4608);
+    stw = (float*)(p + l.stem);
     stb = stw + 216;
-    red = (float*)(p + 5632);
-    bar = (uint64_t*)(p + 9728);
-    tslot = (uint32_t*)(p + 9792);
+    red = (float*)(p + l.red);
+    b2 = (float*)(p + l.b2);
+    rb = (float*)(p + l.rb);
+    sm = (float*)(p + l.sm);
+    sr = (float*)(p + l.sr);
   }
 };
 
@@ -430,9 +472,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int nsteps = a.nsteps, T = a.L.terms;
   const int in_bytes = STEM ? 3 * (2 * a.band + 6) * (a.w + 16) * 2 : 0;
-  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes, T);
+  constexpr MiscLayout ML = misc_layout(CI, true, F8);
+  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes, T, ML.total);
   const size_t lo_off = (size_t)4 * G * a.PIXA * 16;  // low-term planes follow the high-term ones
-  Misc M(sm + L.off_misc, CI);
+  Misc M(sm + L.off_misc, ML, CI);
   unsigned char* x0 = sm + L.off_x0;
   unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -454,6 +497,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
+  for (int i = tid; i < CO; i += blockDim.x) {
+    M.b2[i] = a.b2[i];
+    M.rb[i] = a.rb[i];
+    M.sm[i] = F8 ? a.L.swm[i] : 1.f;
+    M.sr[i] = F8 ? a.L.swr[i] : 1.f;
+  }
   if (STEM) {
     for (int i = tid; i < 216; i += blockDim.x) M.stw[i] = a.stem_w[i];
     for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
@@ -542,62 +591,95 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
       }
     }
   } else {
-    // the band's rows are contiguous in NHWC: item i is pixel i / G, group i % G
+    // the band's rows are contiguous in NHWC. Item i = (pixel pair i / G,
+    // group i % G): pixels (y, x) and (y, x + 1), x even, land in the two
+    // column-parity planes at the same plane pixel, so one store
+    // instruction touches G planes at consecutive pixels
     const __nv_bfloat16* in = a.in + ((size_t)b * h + y_lo) * w * CI;
-    const int n = (y_hi - y_lo + 1) * w * G;
-    for (int base = tid; base < n; base += 4 * blockDim.x) {
-      uint4 v[4][CG / 8];
+    const int w2 = w / 2, n = (y_hi - y_lo + 1) * w2 * G;
+    for (int base = tid; base < n; base += 2 * blockDim.x) {
+      uint4 v[2][2][CG / 8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int i = base + u * blockDim.x;
-        if (i < n) load_cg<CG>(in + (size_t)i * CG, v[u]);
+      for (int u = 0; u < 2; ++u) {
+        const int i = base + u * blockDim.x;
+        if (i < n) {
+          const __nv_bfloat16* src = in + ((size_t)(i / G) * 2 * G + i % G) * CG;
+          load_cg<CG>(src, v[u][0]);
+          load_cg<CG>(src + CI, v[u][1]);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int i = base + u * blockDim.x;
+      for (int u = 0; u < 2; ++u) {
+        const int i = base + u * blockDim.x;
         if (i >= n) continue;
-        int g = i % G, pos = i / G, y = y_lo + pos / w, x = pos % w;
-        float f[CG];
+        const int g = i % G, pos = i / G, y = y_lo + pos / w2, xp = pos % w2;
+        const int p = ((y >> 1) - oy0 + 1) * WP + xp + 1;
 #pragma unroll
-        for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(v[u][k], f + 8 * k);
+        for (int q = 0; q < 2; ++q) {
+          float f[CG];
 #pragma unroll
-        for (int c = 0; c < CG; ++c) f[c] *= M.sa[g * CG + c];
-        int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
-        store_px<F8>(px(x0, pl, p), f, T, lo_off);
+          for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(v[u][q][k], f + 8 * k);
+#pragma unroll
+          for (int c = 0; c < CG; ++c) f[c] *= M.sa[g * CG + c];
+          store_px<F8>(px(x0, ((y & 1) * 2 + q) * G + g, p), f, T, lo_off);
+        }
       }
     }
   }
   __syncthreads();
-  // 2. stage 1 at the rows the stride-2 taps read: y in [2 oy0 - 1, 2 oy0 + 2 TY - 1]
+  // 2. stage 1 at the rows the stride-2 taps read: y in [2 oy0 - 1, 2 oy0 + 2 TY - 1].
+  // Item = (pixel pair (y, x), (y, x + 1) with x even, group g): the pair
+  // reads columns x - 1 .. x + 2 of three rows, 12 plane pixels for 18 taps.
   {
-    const int y1_lo = max(0, 2 * oy0 - 1), y1_hi = min(h - 1, 2 * oy0 + 2 * TY - 1);
-    for (int i = tid; i < (y1_hi - y1_lo + 1) * w * G; i += blockDim.x) {
-      int g = i % G, pos = i / G, y = y1_lo + pos / w, x = pos % w;
-      float2 acc2[CG / 2];
-#pragma unroll
-      for (int c = 0; c < CG / 2; ++c) acc2[c] = make_float2(M.dwb[g * CG + 2 * c], M.dwb[g * CG + 2 * c + 1]);
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        int pl = ((yy & 1) * 2 + (xx & 1)) * G + g, p = ((yy >> 1) - oy0 + 1) * WP + (xx >> 1) + 1;
-        float f[CG];
-        load_px<F8>(px(x0, pl, p), f, T, lo_off);
-        const float4* wt = (const float4*)&M.dw[t * CI + g * CG];
-#pragma unroll
-        for (int q = 0; q < CG / 4; ++q) {
-          float4 wv = wt[q];
-          ffma2(acc2[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
-          ffma2(acc2[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
-        }
-      }
-      float acc[CG];
+    const int y1_lo = max(0, 2 * oy0 - 1), y1_hi = min(h - 1, 2 * oy0 + 2 * TY - 1), w2 = w / 2;
+    for (int i = tid; i < (y1_hi - y1_lo + 1) * w2 * G; i += blockDim.x) {
+      const int g = i % G, pos = i / G, y = y1_lo + pos / w2, x = 2 * (pos % w2);
+      float2 acc0[CG / 2], acc1[CG / 2];
 #pragma unroll
       for (int c = 0; c < CG / 2; ++c) {
-        acc[2 * c] = fmaxf(acc2[c].x, 0.f);
-        acc[2 * c + 1] = fmaxf(acc2[c].y, 0.f);
+        acc0[c] = make_float2(M.dwb[g * CG + 2 * c], M.dwb[g * CG + 2 * c + 1]);
+        acc1[c] = acc0[c];
       }
-      int pl = ((y & 1) * 2 + (x & 1)) * G + g, p = ((y >> 1) - oy0 + 1) * WP + (x >> 1) + 1;
-      store_px<F8>(px(x1, pl, p), acc, T, lo_off);
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const int yy = y + dy - 1, prow = ((yy >> 1) - oy0 + 1) * WP + 1, pr = (yy & 1) * 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int xx = x - 1 + k;
+          float f[CG];
+          load_px<F8>(px(x0, (pr + (xx & 1)) * G + g, prow + (xx >> 1)), f, T, lo_off);
+          if (k <= 2) {
+            const float4* wt = (const float4*)&M.dw[(dy * 3 + k) * CI + g * CG];
+#pragma unroll
+            for (int q = 0; q < CG / 4; ++q) {
+              const float4 wv = wt[q];
+              ffma2(acc0[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+              ffma2(acc0[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
+            }
+          }
+          if (k >= 1) {
+            const float4* wt = (const float4*)&M.dw[(dy * 3 + k - 1) * CI + g * CG];
+#pragma unroll
+            for (int q = 0; q < CG / 4; ++q) {
+              const float4 wv = wt[q];
+              ffma2(acc1[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+              ffma2(acc1[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
+            }
+          }
+        }
+      }
+      const int p = ((y >> 1) - oy0 + 1) * WP + x / 2 + 1;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float o[CG];
+#pragma unroll
+        for (int c = 0; c < CG / 2; ++c) {
+          const float2 v2 = q ? acc1[c] : acc0[c];
+          o[2 * c] = fmaxf(v2.x, 0.f);
+          o[2 * c + 1] = fmaxf(v2.y, 0.f);
+        }
+        store_px<F8>(px(x1, ((y & 1) * 2 + q) * G + g, p), o, T, lo_off);
+      }
     }
   }
   fence_proxy_async();
@@ -622,9 +704,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
           float o[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[c + j] : 1.f, F8 ? a.L.swr[c + j] : 1.f, a.b2[c + j],
-                               a.rb[c + j])
-                         : 0.f;
+            o[j] = valid ? epi(mv[j], rv[j], M.sm[c + j], M.sr[c + j], M.b2[c + j], M.rb[c + j]) : 0.f;
           if (valid) {
             *(uint4*)(dst + c) = f32_to_bf16x8(o);
             *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
@@ -660,9 +740,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   constexpr int NPH = STACK ? 1 : 4, NM = STACK ? 4 * CO : (CO < 16 ? 16 : CO), PS = STACK ? CO : NM;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int nsteps = a.nsteps, T = a.L.terms;  // K-steps per accumulator
-  const Smem L = smem_layout(NPH * nsteps, NM, G, a.PIXA, 0, T);
+  constexpr MiscLayout ML = misc_layout(CI, false, F8);
+  const Smem L = smem_layout(NPH * nsteps, NM, G, a.PIXA, 0, T, ML.total);
   const size_t lo_off = (size_t)G * a.PIXA * 16;
-  Misc M(sm + L.off_misc, CI);
+  Misc M(sm + L.off_misc, ML, CI);
   unsigned char* x0 = sm + L.off_x0;
   unsigned char* x1 = sm + L.off_x1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -682,6 +763,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
   for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
+  for (int i = tid; i < CO; i += blockDim.x) {
+    M.b2[i] = a.b2[i];
+    M.rb[i] = a.rb[i];
+  }
+  for (int i = tid; i < 4 * PS; i += blockDim.x) {
+    M.sm[i] = F8 ? a.L.swm[i] : 1.f;
+    M.sr[i] = F8 ? a.L.swr[i] : 1.f;
+  }
   if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -798,9 +887,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
             ld_wait();
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              o[j] = valid ? epi(mv[j], rv[j], F8 ? a.L.swm[mc + j] : 1.f, F8 ? a.L.swr[mc + j] : 1.f,
-                                 a.b2[cc + j], a.rb[cc + j])
-                           : 0.f;
+              o[j] = valid ? epi(mv[j], rv[j], M.sm[mc + j], M.sr[mc + j], M.b2[cc + j], M.rb[cc + j]) : 0.f;
               sum[j] += o[j];
             }
             if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
@@ -837,11 +924,7 @@ int cdiv(int a, int b) { return (a + b - 1) / b; }
 // K-steps per accumulator: two 16-byte channel groups per MMA (K = 16 bf16
 // or 32 E4M3). With a single channel group per pixel, pairs of taps share a
 // K-step instead.
-int steps_per_acc(int b, bool f8) {
-  const int G = kBlkCin[b] / (f8 ? 16 : 8);
-  if (kBlkEnc[b] || dec_stacked(kBlkCin[b])) return G == 1 ? 5 : 9 * G / 2;
-  return G == 1 ? 2 : 4 * G / 2;
-}
+int steps_per_acc(int b, bool f8) { return k_steps_per_acc(kBlkCin[b], kBlkEnc[b], f8); }
 
 // Band geometry of one level: the largest band (16, 8, 4, 2 or 1 rows)
 // whose accumulators fit the TMEM columns and whose planes and weights fit
@@ -901,10 +984,11 @@ int geo_policy() {
   return p;
 }
 
-// Plane stride skew in 16-byte pixels. The staging and stage-1 loops give
-// consecutive lanes the `touched` planes of one position, then the next
-// positions; with a plane stride of (8 / touched) mod 8 pixels, the eight
-// 16-byte accesses of each quarter-warp fall in distinct bank groups.
+// Plane stride skew in 16-byte pixels. In the staging and stage-1 loops one
+// instruction gives consecutive lanes the `touched` planes (channel groups)
+// of one plane pixel, then of the next pixels; with a plane stride of
+// (8 / touched) mod 8 pixels, the eight 16-byte accesses of each
+// quarter-warp fall in distinct bank groups.
 int plane_skew(int touched) { return touched >= 8 ? 1 : 8 / touched; }
 
 Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
@@ -919,9 +1003,9 @@ Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
       int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(2 * G);
+      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
       int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
-      g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms).total;
+      g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms, misc_layout(CI, true, f8).total).total;
       g.threads = pass == 0 ? 256 : 512;
       pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
       if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
@@ -945,7 +1029,7 @@ Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
       g.ntile = cdiv(count, 128);
       g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 2);
       g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-      g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms).total;
+      g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms, misc_layout(CI, false, f8).total).total;
       g.threads = pass == 0 ? 256 : 512;
       pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512);
       if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;

@@ -33,7 +33,6 @@ struct TcWeights {
   TcLayer layer[6];
 };
 
-constexpr int kTcMiscBytes = 9856;
 constexpr int kTcMaxSmem = 227 * 1024;
 constexpr int kTcHalfSmem = 113 * 1024;  // two CTAs per SM
 
