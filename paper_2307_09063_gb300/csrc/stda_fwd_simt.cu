@@ -543,12 +543,13 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
 // Output module for bf16 maps: the ECA weights of decoder block 3 are folded
 // into the conv weights of each window (the conv is linear in its input) and
 // kept in registers as channel pairs. A CTA takes one window and a band of
-// kOutRows output rows; each thread owns one column and walks down the input
-// rows, loading the three pixels (x - 1, x, x + 1; 16 bytes = 8 channels
-// each) of a row once, one row ahead of use. Input row r feeds the
-// accumulators of output rows r + 1, r and r - 1 (kernel rows 0, 1, 2);
-// after row r, output row r - 1 is complete.
-constexpr int kOutRows = 32;
+// kOutRows output rows and streams the input rows through a shared-memory
+// ring with asynchronous copies issued kOutAhead rows ahead of use (each
+// row: W pixels x 16 bytes = 8 channels, with a zero pixel either side).
+// Each thread owns one column: input row r feeds the accumulators of output
+// rows r + 1, r and r - 1 (kernel rows 0, 1, 2); after row r, output row
+// r - 1 is complete.
+constexpr int kOutRows = 32, kOutAhead = 6, kOutRing = kOutAhead + 2;
 
 __device__ __forceinline__ void out_row(const uint4 (&u)[3], const float2* wr, int dy, float2& acc) {
 #pragma unroll
@@ -562,11 +563,41 @@ __device__ __forceinline__ void out_row(const uint4 (&u)[3], const float2* wr, i
   }
 }
 
+// 16-byte asynchronous global -> shared copy; zero-fills when !valid.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a) {
+  extern __shared__ __align__(16) uint4 ring[];  // [kOutRing][W + 2]
   __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
   __shared__ float s_w[72];
-  const int b = blockIdx.y, H = a.H, W = a.W;
+  const int b = blockIdx.y, H = a.H, W = a.W, RW = W + 2;
   const int y0 = blockIdx.x * kOutRows, y1 = min(H, y0 + kOutRows);
+  const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
+  __nv_bfloat16* out = a.out + (size_t)b * H * W;
+  // rows y0 - 1 .. y1 pass through the ring; row r sits in slot (r - y0 + 1) % kOutRing
+  auto fetch = [&](int r) {
+    if (r <= y1) {
+      uint4* dst = ring + ((r - y0 + 1) % kOutRing) * RW + 1;
+      const bool in = r >= 0 && r < H;
+      for (int x = threadIdx.x; x < W; x += blockDim.x)
+        cp_async16(dst + x, in ? (const void*)(A + ((size_t)r * W + x) * 8) : (const void*)A, in);
+    }
+    cp_async_commit();  // one group per row (empty past the band) keeps the wait count fixed
+  };
+  for (int i = threadIdx.x; i < kOutRing; i += blockDim.x) {
+    ring[i * RW] = make_uint4(0, 0, 0, 0);
+    ring[i * RW + W + 1] = make_uint4(0, 0, 0, 0);
+  }
+  for (int k = 0; k < kOutAhead; ++k) fetch(y0 - 1 + k);
   eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_tmp, s_g, s_s);
   for (int i = threadIdx.x; i < 72; i += blockDim.x) s_w[i] = a.w.out_w[i] * s_s[i & 7];
   __syncthreads();
@@ -574,45 +605,47 @@ __global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a)
 #pragma unroll
   for (int i = 0; i < 36; ++i) wr[i] = make_float2(s_w[2 * i], s_w[2 * i + 1]);
   const float bias = a.w.out_b[0];
-  const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
-  __nv_bfloat16* out = a.out + (size_t)b * H * W;
-  auto load_row = [&](int r, int x, uint4(&u)[3]) {
+  // acc[j][0..2]: output rows r - 1, r, r + 1 of column threadIdx.x + j * blockDim.x
+  constexpr int kCols = 2;  // W <= kCols * blockDim.x
+  float2 acc[kCols][3];
 #pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      const int xx = x + dx - 1;
-      u[dx] = (r >= 0 && r < H && xx >= 0 && xx < W) ? *(const uint4*)(A + ((size_t)r * W + xx) * 8)
-                                                      : make_uint4(0, 0, 0, 0);
-    }
-  };
-  for (int x = threadIdx.x; x < W; x += blockDim.x) {
-    // acc[0], acc[1], acc[2]: output rows r - 1, r, r + 1 while reading row r
-    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    uint4 cur[3], nxt[3];
-    load_row(y0 - 1, x, cur);
-    for (int r = y0 - 1; r <= y1; ++r) {
-      if (r < y1) load_row(r + 1, x, nxt);
-      out_row(cur, wr, 2, acc[0]);
-      out_row(cur, wr, 1, acc[1]);
-      out_row(cur, wr, 0, acc[2]);
+  for (int j = 0; j < kCols; ++j)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[j][q] = make_float2(0.f, 0.f);
+  for (int r = y0 - 1; r <= y1; ++r) {
+    fetch(r + kOutAhead);
+    cp_async_wait<kOutAhead>();  // row r has landed (this thread's copies)
+    __syncthreads();             // ... and every thread's
+    const uint4* row = ring + ((r - y0 + 1) % kOutRing) * RW;
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      const int x = threadIdx.x + j * blockDim.x;
+      if (x >= W) break;
+      const uint4 u[3] = {row[x], row[x + 1], row[x + 2]};
+      out_row(u, wr, 2, acc[j][0]);
+      out_row(u, wr, 1, acc[j][1]);
+      out_row(u, wr, 0, acc[j][2]);
       if (r - 1 >= y0) {
-        const float z = acc[0].x + acc[0].y + bias;
+        const float z = acc[j][0].x + acc[j][0].y + bias;
         out[(size_t)(r - 1) * W + x] = __float2bfloat16_rn(1.f / (1.f + expf(-z)));
       }
-      acc[0] = acc[1];
-      acc[1] = acc[2];
-      acc[2] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) cur[dx] = nxt[dx];
+      acc[j][0] = acc[j][1];
+      acc[j][1] = acc[j][2];
+      acc[j][2] = make_float2(0.f, 0.f);
     }
   }
+  cp_async_wait<0>();
 }
 
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
                             __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook) {
   OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
   const int threads = std::min(kThreads, (W + 31) / 32 * 32);
+  if (W > 2 * threads) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kOutRing * (W + 2) * 16;
   hook->begin(K_OUT, st);
-  k_out_bf16<<<dim3(cdiv(H, kOutRows), B), threads, 0, st>>>(a);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_out_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_out_bf16<<<dim3(cdiv(H, kOutRows), B), threads, smem, st>>>(a);
   hook->end(st);
   return cudaGetLastError();
 }

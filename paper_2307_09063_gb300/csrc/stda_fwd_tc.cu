@@ -960,16 +960,16 @@ void pick_buffers(Geo& g, int cpt, int budget) {
   g.cols = pow2_cols(std::max(g.nbuf, 1) * g.nslot * cpt);
 }
 
-// Tuning override: STDA_TC_BANDS="e1,e2,e3,d1,d2,d3" caps each level's band
-// height (0 = automatic). The geometry rules still apply.
-int band_cap(int b) {
-  static int caps[6] = {-1, -1, -1, -1, -1, -1};
-  if (caps[0] < 0) {
-    for (int& c : caps) c = 0;
-    if (const char* e = getenv("STDA_TC_BANDS")) sscanf(e, "%d,%d,%d,%d,%d,%d", &caps[0], &caps[1], &caps[2],
-                                                        &caps[3], &caps[4], &caps[5]);
+// Tuning override: STDA_TC_BANDS="e1,e2,e3,d1,d2,d3" sets each level's band
+// height (1 .. 16 rows; 0 = automatic) where that band fits.
+int band_override(int b) {
+  static int v[6] = {-1, -1, -1, -1, -1, -1};
+  if (v[0] < 0) {
+    for (int& c : v) c = 0;
+    if (const char* e = getenv("STDA_TC_BANDS")) sscanf(e, "%d,%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]);
+    for (int& c : v) c = (c >= 1 && c <= 16) ? c : 0;
   }
-  return caps[b];
+  return v[b];
 }
 
 // Geometry policy: 0 = the largest band first (default; the faster one
@@ -991,51 +991,63 @@ int geo_policy() {
 // quarter-warp fall in distinct bank groups.
 int plane_skew(int touched) { return touched >= 8 ? 1 : 8 / touched; }
 
-Geo encoder_geo(int b, bool f8, int terms, int h, int w) {
+// One candidate geometry: band height TA (output rows for the encoder, input
+// rows for the decoder) and CTA shape (pass 0: two CTAs of 256 threads per
+// SM, shared memory <= half, TMEM <= 256 columns; pass 1: one CTA of 512
+// threads). band = 0 if it does not fit.
+Geo encoder_geo_at(int b, bool f8, int terms, int w, int TY, int pass) {
   const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
   const bool stem = b == 0;
   Geo g{};
-  for (int it = 0; it < 10; ++it) {
-      const int pass = geo_policy() ? it / 5 : it % 2, TY = 16 >> (geo_policy() ? it % 5 : it / 2);
-      if (band_cap(b) && TY > band_cap(b)) continue;
-      g.band = TY;
-      g.WP = wo + 2;
-      int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
-      g.ntile = cdiv(count, 128);
-      g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
-      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-      int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
-      g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms, misc_layout(CI, true, f8).total).total;
-      g.threads = pass == 0 ? 256 : 512;
-      pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
-      if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
-    }
-  g.band = 0;
+  g.band = TY;
+  g.WP = wo + 2;
+  const int m_lo = g.WP + 1, count = TY * g.WP + wo - m_lo + 1;
+  g.ntile = cdiv(count, 128);
+  g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
+  g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
+  const int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
+  g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms, misc_layout(CI, true, f8).total).total;
+  g.threads = pass == 0 ? 256 : 512;
+  pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
+  if (!g.nbuf || g.smem > (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) g.band = 0;
   return g;
 }
 
-Geo decoder_geo(int b, bool f8, int terms, int h, int w) {
+Geo decoder_geo_at(int b, bool f8, int terms, int w, int TA, int pass) {
   const int CI = kBlkCin[b], CO = CI / 2, G = CI / (f8 ? 16 : 8), NP = CO < 16 ? 16 : CO,
             nsteps = steps_per_acc(b, f8);
   const bool stack = dec_stacked(CI);
   const int nph = stack ? 1 : 4, NM = stack ? 4 * CO : NP;  // accumulators per branch, N per MMA
   Geo g{};
-  for (int it = 0; it < 10; ++it) {
-      const int pass = geo_policy() ? it / 5 : it % 2, TA = 16 >> (geo_policy() ? it % 5 : it / 2);
-      if (band_cap(b) && TA > band_cap(b)) continue;
-      g.band = TA;
-      g.WP = w + 4;
-      int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
-      g.ntile = cdiv(count, 128);
-      g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 2);
-      g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-      g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms, misc_layout(CI, false, f8).total).total;
-      g.threads = pass == 0 ? 256 : 512;
-      pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512);
-      if (g.nbuf && g.smem <= (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) return g;
-    }
-  g.band = 0;
+  g.band = TA;
+  g.WP = w + 4;
+  const int m_lo = 2 * g.WP + 2, count = (TA - 1) * g.WP + w;
+  g.ntile = cdiv(count, 128);
+  g.PIXA = std::max((TA + 4) * g.WP, m_lo + 128 * g.ntile + g.WP + 2);
+  g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
+  g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms, misc_layout(CI, false, f8).total).total;
+  g.threads = pass == 0 ? 256 : 512;
+  pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512);
+  if (!g.nbuf || g.smem > (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) g.band = 0;
   return g;
+}
+
+Geo level_geo(int b, bool f8, int terms, int h, int w) {
+  auto at = [&](int TA, int pass) {
+    return kBlkEnc[b] ? encoder_geo_at(b, f8, terms, w, TA, pass) : decoder_geo_at(b, f8, terms, w, TA, pass);
+  };
+  if (const int TA = band_override(b)) {
+    for (int pass = 0; pass < 2; ++pass) {
+      Geo g = at(TA, pass);
+      if (g.band) return g;
+    }
+  }
+  for (int it = 0; it < 10; ++it) {
+    const int pass = geo_policy() ? it / 5 : it % 2, TA = 16 >> (geo_policy() ? it % 5 : it / 2);
+    Geo g = at(TA, pass);
+    if (g.band) return g;
+  }
+  return Geo{};
 }
 
 int sm_count() {
@@ -1250,7 +1262,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     const int h = H / in_div[l], wd = W / in_div[l];
     const bool f8 = tw.layer[l].f8;
     const int terms = tw.layer[l].terms;
-    Geo g = kBlkEnc[l] ? encoder_geo(l, f8, terms, h, wd) : decoder_geo(l, f8, terms, h, wd);
+    Geo g = level_geo(l, f8, terms, h, wd);
     if (g.band == 0) return cudaErrorInvalidConfiguration;
     TcArgs a{};
     a.in = (const __nv_bfloat16*)(l == 0 ? (const void*)in : prev);
