@@ -202,25 +202,32 @@ __device__ __forceinline__ void warp_sums_to(float* v, float* dst) {
     for (int j = 0; j < R; ++j) dst[base + j] += v[j];
 }
 
-// OR of `pred` over the 128 threads of warp group g (named barrier 1 + g,
-// g < 4); also orders the group's threads like a barrier.
-template <int ID>
+// OR of `pred` over the threads of TMEM buffer b's warp groups (named
+// barrier 1 + b, b < 4; 128 or 256 threads); also orders those threads like
+// a barrier.
+template <int ID, int COUNT>
 __device__ __forceinline__ uint32_t bar_red_or(uint32_t pred) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\t"
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, %3, q;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(r)
-      : "r"(pred), "n"(ID)
+      : "r"(pred), "n"(ID), "n"(COUNT)
       : "memory");
   return r;
 }
-__device__ __forceinline__ bool group_or(bool pred, int g) {
-  switch (g) {
-    case 0: return bar_red_or<1>(pred) != 0;
-    case 1: return bar_red_or<2>(pred) != 0;
-    case 2: return bar_red_or<3>(pred) != 0;
-    default: return bar_red_or<4>(pred) != 0;
+__device__ __forceinline__ bool buffer_or(bool pred, int b, int groups) {
+  if (groups == 2) {
+    switch (b) {
+      case 0: return bar_red_or<1, 256>(pred) != 0;
+      default: return bar_red_or<2, 256>(pred) != 0;
+    }
+  }
+  switch (b) {
+    case 0: return bar_red_or<1, 128>(pred) != 0;
+    case 1: return bar_red_or<2, 128>(pred) != 0;
+    case 2: return bar_red_or<3, 128>(pred) != 0;
+    default: return bar_red_or<4, 128>(pred) != 0;
   }
 }
 
@@ -377,6 +384,13 @@ struct Misc {
   }
 };
 
+// Stage-1 weights of tap t, channels 4q .. 4q + 3 of group g (layout
+// [tap][quad][group][4]).
+template <int CG>
+__device__ __forceinline__ float4 dw_quad(const float* dw, int t, int q, int g, int G) {
+  return *(const float4*)&dw[((t * (CG / 4) + q) * G + g) * 4];
+}
+
 __device__ void copy_to_smem(void* dst, const void* src, int bytes) {
   const uint4* s = (const uint4*)src;
   uint4* d = (uint4*)dst;
@@ -405,60 +419,63 @@ __device__ __forceinline__ float epi(float m, float r, float sm, float sr, float
   return fmaxf(m * sm + b2, 0.f) + r * sr + rb;
 }
 
-// The tiles of one item. Warp group g (< a.nbuf) owns the TMEM slots
-// (g * nslot + s) * cpt, s < nslot, their mbarriers 2 g + s and the tiles
-// g, g + nbuf, ...: its first thread issues a tile's MMAs and commits them,
-// the four warps drain the accumulators (warp 4 g + q reads TMEM lanes
-// 32 q .. 32 q + 31) through drain(tile, column). With two slots the next
+// The tiles of one item. TMEM buffer b (< a.nbuf) has a.gpb warp groups
+// (1 or 2; group g serves buffer g / gpb as part g % gpb), slots
+// (b * nslot + s) * cpt, s < nslot, mbarriers 2 b + s and the tiles b,
+// b + nbuf, ...: the first thread of its part-0 group issues a tile's MMAs
+// and commits them, its groups drain the accumulators (warp 4 g + q reads
+// TMEM lanes 32 q .. 32 q + 31; with two groups each drains its part of the
+// columns) through drain(tile, column, part, parts). With two slots the next
 // tile is queued before the drain, so the tensor core runs it meanwhile;
-// groups run unsynchronised, so one group's drain also overlaps other
-// groups' MMAs. Bounded waits; a timeout is agreed per group (the issuer
+// buffers run unsynchronised, so one buffer's drain also overlaps other
+// buffers' MMAs. Bounded waits; a timeout is agreed per buffer (the issuer
 // gives its queued MMAs a second bounded wait) and returned as false.
-// `phases` holds bit 2 g + s = parity of that barrier's next completion.
+// `phases` holds bit 2 b + s = parity of that barrier's next completion.
 template <bool F8, typename Drain>
 __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32_t tmem, uint32_t& phases,
                                           int cpt, int nsteps, int nph, int NM, int T, uint32_t a_lo,
                                           uint32_t b_lo, Drain drain) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = warp >> 2, ng = a.nbuf, ns = a.nslot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gpb = a.gpb;
+  const int bi = (warp >> 2) / gpb, part = (warp >> 2) % gpb, nb = a.nbuf, ns = a.nslot;
   bool ok = true;
-  if (g < ng) {
-    const bool issuer = (warp & 3) == 0 && lane == 0;
-    uint32_t par = (phases >> (2 * g)) & 3u;
+  if (bi < nb) {
+    const bool issuer = part == 0 && (warp & 3) == 0 && lane == 0;
+    uint32_t par = (phases >> (2 * bi)) & 3u;
     auto issue = [&](int tile, int s) {
       fence_after_sync();
-      issue_tile<F8>(tmem + (uint32_t)((g * ns + s) * cpt), M.dtab, nsteps, nph, NM, (uint32_t)(128 * tile), T,
+      issue_tile<F8>(tmem + (uint32_t)((bi * ns + s) * cpt), M.dtab, nsteps, nph, NM, (uint32_t)(128 * tile), T,
                      a_lo, b_lo);
-      commit(M.bar + 2 * g + s);
+      commit(M.bar + 2 * bi + s);
     };
-    if (issuer && g < a.ntile) issue(g, 0);
+    if (issuer && bi < a.ntile) issue(bi, 0);
     int k = 0;
-    for (int i = g; i < a.ntile; i += ng, ++k) {
+    for (int i = bi; i < a.ntile; i += nb, ++k) {
       const int s = ns == 2 ? (k & 1) : 0;
-      const bool next = i + ng < a.ntile;
-      if (ns == 2 && issuer && next) issue(i + ng, s ^ 1);
+      const bool next = i + nb < a.ntile;
+      if (ns == 2 && issuer && next) issue(i + nb, s ^ 1);
       __syncwarp();
-      ok = mbar_wait(M.bar + 2 * g + s, (par >> s) & 1u);
+      ok = mbar_wait(M.bar + 2 * bi + s, (par >> s) & 1u);
       par ^= 1u << s;
       fence_after_sync();
-      if (ok) drain(i, (uint32_t)((g * ns + s) * cpt));
-      // the group has read the slot before a later tile overwrites it
+      if (ok) drain(i, (uint32_t)((bi * ns + s) * cpt), part, gpb);
+      // the buffer's groups have read the slot before a later tile overwrites it
       fence_before_sync();
-      if (group_or(!ok, g)) {
+      if (buffer_or(!ok, bi, gpb)) {
         if (issuer) {
-          mbar_wait(M.bar + 2 * g + s, ((par >> s) & 1u) ^ 1u);
-          if (ns == 2 && next) mbar_wait(M.bar + 2 * g + (s ^ 1), (par >> (s ^ 1)) & 1u);
+          mbar_wait(M.bar + 2 * bi + s, ((par >> s) & 1u) ^ 1u);
+          if (ns == 2 && next) mbar_wait(M.bar + 2 * bi + (s ^ 1), (par >> (s ^ 1)) & 1u);
         }
         ok = false;
         break;
       }
-      if (ns == 1 && issuer && next) issue(i + ng, 0);
+      if (ns == 1 && issuer && next) issue(i + nb, 0);
     }
   }
   // every thread advances every barrier's phase by the commits of this item
-  for (int gg = 0; gg < ng; ++gg) {
-    const int n = gg < a.ntile ? (a.ntile - 1 - gg) / ng + 1 : 0;
+  for (int bb = 0; bb < nb; ++bb) {
+    const int n = bb < a.ntile ? (a.ntile - 1 - bb) / nb + 1 : 0;
     const int n0 = ns == 2 ? (n + 1) / 2 : n, n1 = ns == 2 ? n / 2 : 0;
-    phases ^= ((uint32_t)(n0 & 1) << (2 * gg)) | ((uint32_t)(n1 & 1) << (2 * gg + 1));
+    phases ^= ((uint32_t)(n0 & 1) << (2 * bb)) | ((uint32_t)(n1 & 1) << (2 * bb + 1));
   }
   return ok;
 }
@@ -495,7 +512,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   const int m_lo = WP + 1;
   fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, 1, NP, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
-  for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
+  // stage-1 weights as [tap][quad][group][4]: the lanes of one plane pixel
+  // (consecutive groups) read consecutive 16-byte quads
+  for (int i = tid; i < 9 * CI; i += blockDim.x) {
+    const int t = i / CI, gq = (i % CI) / 4, e = i % 4;
+    M.dw[((t * (CG / 4) + gq % (CG / 4)) * G + gq / (CG / 4)) * 4 + e] = a.dw[i];
+  }
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
   for (int i = tid; i < CO; i += blockDim.x) {
     M.b2[i] = a.b2[i];
@@ -649,19 +671,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
           float f[CG];
           load_px<F8>(px(x0, (pr + (xx & 1)) * G + g, prow + (xx >> 1)), f, T, lo_off);
           if (k <= 2) {
-            const float4* wt = (const float4*)&M.dw[(dy * 3 + k) * CI + g * CG];
 #pragma unroll
             for (int q = 0; q < CG / 4; ++q) {
-              const float4 wv = wt[q];
+              const float4 wv = dw_quad<CG>(M.dw, dy * 3 + k, q, g, G);
               ffma2(acc0[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
               ffma2(acc0[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
             }
           }
           if (k >= 1) {
-            const float4* wt = (const float4*)&M.dw[(dy * 3 + k - 1) * CI + g * CG];
 #pragma unroll
             for (int q = 0; q < CG / 4; ++q) {
-              const float4 wv = wt[q];
+              const float4 wv = dw_quad<CG>(M.dw, dy * 3 + k - 1, q, g, G);
               ffma2(acc1[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
               ffma2(acc1[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
             }
@@ -690,7 +710,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   const int cpt = 2 * NP;  // TMEM columns per tile
   const bool ok = run_tiles<F8>(
       a, M, tmem, phases, cpt, nsteps, 1, NP, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
-      [&](int i, uint32_t col) {
+      [&](int i, uint32_t col, int, int) {  // encoders drain a tile with one group
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
         int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
         bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
@@ -761,7 +781,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   const int m_lo = 2 * WP + 2;
   fill_desc_table<F8>(M.dtab, a.L.ks, nsteps, NPH, NM, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
                       smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
-  for (int i = tid; i < 9 * CI; i += blockDim.x) M.dw[i] = a.dw[i];
+  // stage-1 weights as [tap][quad][group][4]: the lanes of one plane pixel
+  // (consecutive groups) read consecutive 16-byte quads
+  for (int i = tid; i < 9 * CI; i += blockDim.x) {
+    const int t = i / CI, gq = (i % CI) / 4, e = i % 4;
+    M.dw[((t * (CG / 4) + gq % (CG / 4)) * G + gq / (CG / 4)) * 4 + e] = a.dw[i];
+  }
   for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
   for (int i = tid; i < CO; i += blockDim.x) {
     M.b2[i] = a.b2[i];
@@ -842,10 +867,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
       for (int t = 0; t < 9; ++t) {
         float f[CG];
         load_px<F8>(px(x0, g, p + (t / 3 - 1) * WP + t % 3 - 1), f, T, lo_off);
-        const float4* wt = (const float4*)&M.dw[t * CI + g * CG];
 #pragma unroll
         for (int q = 0; q < CG / 4; ++q) {
-          float4 wv = wt[q];
+          const float4 wv = dw_quad<CG>(M.dw, t, q, g, G);
           ffma2(acc2[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
           ffma2(acc2[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
         }
@@ -867,7 +891,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   const int cpt = 2 * NPH * NM;  // TMEM columns per tile: (main, residual) x 4 phases
   const bool ok = run_tiles<F8>(
       a, M, tmem, phases, cpt, nsteps, NPH, NM, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
-      [&](int i, uint32_t col) {
+      [&](int i, uint32_t col, int part, int parts) {  // part p of `parts` drains phases 4p/parts ..
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
         int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
         bool valid = lr >= 2 && lr < TA + 2 && r < h && c >= 0 && c < w;
@@ -878,6 +902,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
           float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int ph = 0; ph < 4; ++ph) {
+            if (ph * parts / 4 != part) continue;
             int Y = 2 * r + (ph >> 1), X = 2 * c + (ph & 1);
             __nv_bfloat16* dst = a.out + (((size_t)b * Ho + Y) * Wo + X) * CO;
             float mv[8], rv[8], o[8];
@@ -931,7 +956,7 @@ int steps_per_acc(int b, bool f8) { return k_steps_per_acc(kBlkCin[b], kBlkEnc[b
 // shared memory; at equal band, two CTAs of 256 threads per SM (shared
 // memory <= half, TMEM <= 256 columns) before one CTA of 512 threads.
 struct Geo {
-  int band, ntile, WP, PIXA, smem, threads, nbuf, nslot;
+  int band, ntile, WP, PIXA, smem, threads, nbuf, nslot, gpb;
   uint32_t cols;
 };
 
@@ -945,18 +970,22 @@ int max_slots() {
   return m;
 }
 
-// Warp groups running tiles: as many as fit the TMEM column budget; then a
-// second slot per group if every group can have one.
-void pick_buffers(Geo& g, int cpt, int budget) {
+// TMEM buffers: one per warp group where the column budget allows, then a
+// second slot per buffer if every group can have one. With split = true
+// (decoders) and half as many buffers as groups, two groups share each
+// buffer and split its drain.
+void pick_buffers(Geo& g, int cpt, int budget, bool split = false) {
   const int groups = g.threads / 128;
   g.nbuf = 0;
   g.nslot = 1;
+  g.gpb = 1;
   for (int k = groups; k >= 1; --k)
     if ((int)pow2_cols(k * cpt) <= budget) {
       g.nbuf = k;
       break;
     }
   if (max_slots() == 2 && g.nbuf == groups && (int)pow2_cols(2 * groups * cpt) <= budget) g.nslot = 2;
+  if (split && g.nbuf && 2 * g.nbuf == groups && g.nbuf <= 2) g.gpb = 2;
   g.cols = pow2_cols(std::max(g.nbuf, 1) * g.nslot * cpt);
 }
 
@@ -1027,7 +1056,7 @@ Geo decoder_geo_at(int b, bool f8, int terms, int w, int TA, int pass) {
   g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
   g.smem = smem_layout(nph * nsteps, NM, G, g.PIXA, 0, terms, misc_layout(CI, false, f8).total).total;
   g.threads = pass == 0 ? 256 : 512;
-  pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512);
+  pick_buffers(g, 2 * nph * NM, pass == 0 ? 256 : 512, true);
   if (!g.nbuf || g.smem > (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) g.band = 0;
   return g;
 }
@@ -1287,6 +1316,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.tmem_cols = g.cols;
     a.nbuf = g.nbuf;
     a.nslot = g.nslot;
+    a.gpb = g.gpb;
     a.stem_w = w.stem_w;
     a.stem_b = w.stem_b;
     a.dw = w.blk[l].dw;

@@ -51,8 +51,9 @@ struct TcArgs {
   int WP, PIXA;   // plane pitch and pixels per plane
   int tiles_per_window;
   int nwin;  // windows in the batch (items = windows x bands)
-  int nbuf;   // warp groups that run tiles (1 .. 4), one MMA issuer each
-  int nslot;  // TMEM accumulator slots per group (2: next tile queued before the drain)
+  int nbuf;   // TMEM buffers that run tiles (1 .. 4), one MMA issuer each
+  int nslot;  // TMEM accumulator slots per buffer (2: next tile queued before the drain)
+  int gpb;    // warp groups per TMEM buffer (2: the drain is split between them)
   int nsteps;
   uint32_t tmem_cols;
   const float *stem_w, *stem_b, *dw, *dwb, *b2, *rb;
