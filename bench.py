@@ -13,8 +13,10 @@ no code), on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -46,6 +48,26 @@ KERNEL_TC_MACS_PER_PX = {"enc1_stem": 576, "enc2": 576, "enc3": 576, "dec1": 102
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.070
 FFMA_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ / 1e3  # 80.5
 FP8_OVER_BF16 = 4.5 / 2.25  # nominal dense ratio
+
+
+def ncu_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload (profiles/ncu_tc_<workload>.md), or None when there is none or
+    a kernel source changed since the capture (its sha256 differs)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_tc_{workload}.md")
+    try:
+        with open(path) as f:
+            m = re.search(r"<!-- traffic (\{.*?\}) -->", f.read())
+        rec = json.loads(m.group(1)) if m else None
+        if not rec or rec.get("kernel") != kernel:
+            return None
+        for src, digest in rec["sources"].items():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def load_peaks():
@@ -430,7 +452,7 @@ def main():
     else:
         bound, ach, peak, psrc = "alu", alu_tf, FFMA_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
     roofline = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_source": psrc,
+                "frac": ach / peak, "traffic": ncu_traffic(w.name, name), "peak_source": psrc,
                 "alu": {"achieved": alu_tf, "peak": FFMA_PEAK_TFLOPS, "frac": fr_alu,
                         "flops_per_launch": 2.0 * fma_macs * px},
                 "tensor": {"achieved": tc_tf, "peak": tc_peak, "frac": fr_tc, "flops_per_launch": 2.0 * tc_macs * px},
