@@ -105,6 +105,37 @@ size_t stda_num_buffers(void);
 stda_status stda_init_params(uint64_t seed, float* host_params,
                              float* host_buffers);
 
+/* Structural re-parameterisation for deployment (host only, no GPU). The
+ * paper's blocks train as multi-branch MobileOne-style units (Sec. IV-B,
+ * Eqs. "mobile_encoder_stage1/2", "mobile_decoder_stage1/2": dw 1x1 + BN,
+ * dw 3x3 + BN and an identity BN summed before a ReLU; a conv + BN main
+ * branch) and collapse at inference into one conv + bias per branch. This
+ * writes that inference network, with every BN folded in FP64 and rounded
+ * to float once, in PyTorch weight layouts, concatenated in this order:
+ *   stem.weight [8][3][3][3], stem.bias [8]      Conv2d(3, 8, 3, padding 1) + ReLU
+ *   for each block b = 0..5 (Cin 8,16,32,64,32,16; Cout 16,32,64,32,16,8):
+ *     dw.weight [Cin][1][3][3], dw.bias [Cin]    depthwise Conv2d(padding 1,
+ *                                                groups Cin) + ReLU (the
+ *                                                decoder's stride-1 transposed
+ *                                                conv written as a correlation)
+ *     main.weight, main.bias [Cout]              encoder: Conv2d [Cout][Cin][3][3],
+ *                                                stride 2, padding 1; decoder:
+ *                                                ConvTranspose2d [Cin][Cout][4][4],
+ *                                                stride 2, padding 1; then ReLU
+ *     res.weight, res.bias [Cout]                the same conv shape, no ReLU;
+ *                                                y = ReLU(main) + res
+ *     eca.weight [1][1][3]                       Conv1d(1, 1, 3, padding 1, no
+ *                                                bias) on the channel means,
+ *                                                sigmoid, scales y
+ *   out.weight [1][8][3][3], out.bias [1]        Conv2d(8, 1, 3, padding 1) + sigmoid
+ * with the skips D1 += E2 (input of block 4) and D2 += E1 (input of block 5)
+ * after ECA. host_params / host_buffers as for stda_init_params; host_out
+ * holds n = stda_reparam_count() floats. Returns STDA_ERR_INVALID_ARG on a null
+ * pointer or a wrong n. */
+size_t stda_reparam_count(void);
+stda_status stda_reparam_export(const float* host_params, const float* host_buffers,
+                                float* host_out, size_t n);
+
 /* Copies the FP32 parameters / BN buffers to or from host memory (n must
  * equal the count above). stda_set_* refolds BN into the convolutions in
  * FP64 on the host and re-uploads every precision's weights. */

@@ -257,6 +257,70 @@ void fold_params(const float* params, const float* buffers, float* dst, FoldedOf
   dst[off->out_b] = (float)ob[0];
 }
 
+// Inference network in PyTorch weight layouts (the order documented with
+// stda_reparam_export), BN folded in FP64 exactly as fold_params does.
+size_t reparam_count() {
+  size_t n = 216 + 8 + 72 + 1;
+  for (int b = 0; b < kNumBlocks; ++b) {
+    const size_t ci = kBlkCin[b], co = kBlkCout[b], dense = (kBlkEnc[b] ? 9 : 16) * ci * co;
+    n += 9 * ci + ci + 2 * dense + 2 * co + 3;
+  }
+  return n;
+}
+
+void reparam_export(const float* params, const float* buffers, float* out) {
+  Cursor c{params};
+  const float* bq = buffers;
+  float* o = out;
+  {
+    auto w = c.take(216);
+    auto g = c.take(8);
+    auto be = c.take(8);
+    BnFold f = bn_fold(g, be, bq, 8);
+    for (int oc = 0; oc < 8; ++oc)
+      for (int k = 0; k < 27; ++k) *o++ = (float)(w[oc * 27 + k] * f.s[oc]);
+    for (int oc = 0; oc < 8; ++oc) *o++ = (float)f.t[oc];
+  }
+  for (int b = 0; b < kNumBlocks; ++b) {
+    const int ci = kBlkCin[b], co = kBlkCout[b];
+    const bool enc = kBlkEnc[b];
+    const int dense = enc ? co * ci * 9 : ci * co * 16;
+    auto w1 = c.take(ci);
+    auto g1 = c.take(ci), b1 = c.take(ci);
+    auto w3 = c.take(9 * ci);
+    auto g2 = c.take(ci), b2 = c.take(ci);
+    auto g3 = c.take(ci), b3 = c.take(ci);
+    auto w2 = c.take(dense);
+    auto g = c.take(co), be = c.take(co);
+    auto rw = c.take(dense);
+    auto rb = c.take(co);
+    auto eca = c.take(3);
+    BnFold f1 = bn_fold(g1, b1, bq, ci), f2 = bn_fold(g2, b2, bq, ci), f3 = bn_fold(g3, b3, bq, ci);
+    BnFold fm = bn_fold(g, be, bq, co);
+    for (int ch = 0; ch < ci; ++ch)
+      for (int t = 0; t < 9; ++t) {
+        double k = f2.s[ch] * w3[ch * 9 + (enc ? t : 8 - t)];
+        if (t == 4) k += f1.s[ch] * w1[ch] + f3.s[ch];
+        *o++ = (float)k;
+      }
+    for (int ch = 0; ch < ci; ++ch) *o++ = (float)(f1.t[ch] + f2.t[ch] + f3.t[ch]);
+    // main conv: the output channel is the first index of a Conv2d weight,
+    // the second of a ConvTranspose2d weight
+    for (int i = 0; i < dense; ++i) {
+      const int oc = enc ? i / (ci * 9) : (i / 16) % co;
+      *o++ = (float)(w2[i] * fm.s[oc]);
+    }
+    for (int oc = 0; oc < co; ++oc) *o++ = (float)fm.t[oc];
+    for (int i = 0; i < dense; ++i) *o++ = (float)rw[i];
+    for (int oc = 0; oc < co; ++oc) *o++ = (float)rb[oc];
+    for (int j = 0; j < 3; ++j) *o++ = (float)eca[j];
+  }
+  auto ow = c.take(72);
+  auto ob = c.take(1);
+  for (int k = 0; k < 72; ++k) *o++ = (float)ow[k];
+  *o++ = (float)ob[0];
+}
+
 const char* const kKernelNames[K_NUM_IDS] = {"enc1_stem", "enc2", "enc3", "dec1", "dec2", "dec3", "out"};
 
 NetW net_from(const float* base, const FoldedOffsets& o) {
@@ -477,6 +541,14 @@ stda_status stda_destroy(stda_ctx* c) {
 stda_status stda_init_params(uint64_t seed, float* params, float* buffers) {
   if (!params || !buffers) return STDA_ERR_INVALID_ARG;
   stda::init_params(seed, params, buffers);
+  return STDA_OK;
+}
+
+size_t stda_reparam_count(void) { return stda::reparam_count(); }
+
+stda_status stda_reparam_export(const float* params, const float* buffers, float* out, size_t n) {
+  if (!params || !buffers || !out || n != stda::reparam_count()) return STDA_ERR_INVALID_ARG;
+  stda::reparam_export(params, buffers, out);
   return STDA_OK;
 }
 

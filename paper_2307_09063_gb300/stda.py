@@ -60,6 +60,8 @@ def lib():
         for n in ("stda_get_params", "stda_set_params", "stda_get_buffers", "stda_set_buffers"):
             getattr(L, n).argtypes = [_VP, _VP, ctypes.c_size_t]
         L.stda_init_params.argtypes = [ctypes.c_uint64, _VP, _VP]
+        L.stda_reparam_count.restype = ctypes.c_size_t
+        L.stda_reparam_export.argtypes = [_VP, _VP, _VP, ctypes.c_size_t]
         L.stda_forward.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_device_status.argtypes = [_VP]
         L.stda_last_error.restype = ctypes.c_char_p
@@ -115,6 +117,43 @@ def init_params(seed=0):
     if st != OK:
         raise StdaError(st)
     return p, b
+
+
+def reparam_shapes():
+    """(name, shape) of the re-parameterised inference network, in the order
+    of stda_reparam_export (PyTorch Conv2d / ConvTranspose2d / Conv1d
+    weight layouts)."""
+    cin, enc = (8, 16, 32, 64, 32, 16), (1, 1, 1, 0, 0, 0)
+    t = [("stem.weight", (8, 3, 3, 3)), ("stem.bias", (8,))]
+    for b in range(6):
+        ci = cin[b]
+        co = 2 * ci if enc[b] else ci // 2
+        conv = (co, ci, 3, 3) if enc[b] else (ci, co, 4, 4)
+        t += [(f"blk{b}.dw.weight", (ci, 1, 3, 3)), (f"blk{b}.dw.bias", (ci,)),
+              (f"blk{b}.main.weight", conv), (f"blk{b}.main.bias", (co,)),
+              (f"blk{b}.res.weight", conv), (f"blk{b}.res.bias", (co,)),
+              (f"blk{b}.eca.weight", (1, 1, 3))]
+    return t + [("out.weight", (1, 8, 3, 3)), ("out.bias", (1,))]
+
+
+def reparam_export(params, buffers):
+    """Host-side: the re-parameterised inference network (every BN folded,
+    stage-1 branches merged) as {name: float32 array}, through
+    stda_reparam_export."""
+    n = int(lib().stda_reparam_count())
+    out = np.empty(n, np.float32)
+    p = np.ascontiguousarray(params, np.float32)
+    b = np.ascontiguousarray(buffers, np.float32)
+    st = lib().stda_reparam_export(p.ctypes.data, b.ctypes.data, out.ctypes.data, n)
+    if st != OK:
+        raise StdaError(st)
+    d, off = {}, 0
+    for name, shape in reparam_shapes():
+        k = int(np.prod(shape))
+        d[name] = out[off:off + k].reshape(shape)
+        off += k
+    assert off == n
+    return d
 
 
 class Context:
