@@ -220,6 +220,23 @@ def forward(params, buffers, x, return_blocks=False):
     return out, res
 
 
+def num_params_frames(frames):
+    return lib().orc_num_params_frames(frames)
+
+
+def forward_frames(params, buffers, x):
+    """Fusion variant (Sec. IV-A): x[T][H][W] with T = 2..4 stacked maps,
+    params of that variant (stem W[8][T][3][3]) -> z[H][W] (float64)."""
+    params, buffers, x = _f32(params), _f32(buffers), _f32(x)
+    T, H, W = x.shape
+    assert params.size == num_params_frames(T)
+    out = np.empty((H, W))
+    rc = lib().orc_forward_frames(_p(params, _F), _p(buffers, _F), _p(x, _F), T, H, W, _p(out, _D))
+    if rc:
+        raise ValueError(f"oracle forward rejected {T} frames of {H}x{W}")
+    return out
+
+
 def forward_batch(params, buffers, x, nthreads=None):
     """x[B][3][H][W] -> z[B][H][W] (float64), POSIX threads over windows."""
     params, buffers, x = _f32(params), _f32(buffers), _f32(x)

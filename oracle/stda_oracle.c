@@ -428,6 +428,7 @@ typedef struct {
 typedef struct {
   double* pmem;
   double* bmem;
+  int frames; /* input maps per window: stem input channels */
   const double *stem_w, *stem_g, *stem_b, *stem_m, *stem_v;
   orc_blk blk[6];
   const double *out_w, *out_b;
@@ -442,8 +443,10 @@ static int blk_dense(int b) {
   return BLK_ENC[b] ? co * ci * 9 : ci * co * 16;
 }
 
-int orc_num_params(void) {
-  int n = 216 + 16;
+/* The stem weight W[8][T][3][3] grows with the number T of stacked maps;
+ * every other tensor is independent of T. */
+int orc_num_params_frames(int frames) {
+  int n = 8 * frames * 9 + 16;
   for (int b = 0; b < 6; ++b) {
     int ci = BLK_CIN[b], co = blk_cout(b);
     n += ci + 2 * ci + 9 * ci + 2 * ci + 2 * ci + blk_dense(b) + 2 * co + blk_dense(b) + co + 3;
@@ -451,21 +454,24 @@ int orc_num_params(void) {
   return n + 72 + 1;
 }
 
+int orc_num_params(void) { return orc_num_params_frames(3); }
+
 int orc_num_buffers(void) {
   int n = 16;
   for (int b = 0; b < 6; ++b) n += 2 * (3 * BLK_CIN[b] + blk_cout(b));
   return n;
 }
 
-static void net_load(orc_net* net, const float* params, const float* buffers) {
-  int np = orc_num_params(), nb = orc_num_buffers();
+static void net_load_frames(orc_net* net, const float* params, const float* buffers, int frames) {
+  int np = orc_num_params_frames(frames), nb = orc_num_buffers();
+  net->frames = frames;
   net->pmem = malloc(sizeof(double) * np);
   net->bmem = malloc(sizeof(double) * nb);
   for (int i = 0; i < np; ++i) net->pmem[i] = (double)params[i];
   for (int i = 0; i < nb; ++i) net->bmem[i] = (double)buffers[i];
   const double* p = net->pmem;
   const double* q = net->bmem;
-  net->stem_w = p; p += 216;
+  net->stem_w = p; p += 8 * frames * 9;
   net->stem_g = p; p += 8;
   net->stem_b = p; p += 8;
   net->stem_m = q; q += 8;
@@ -499,6 +505,10 @@ static void net_load(orc_net* net, const float* params, const float* buffers) {
   }
   net->out_w = p; p += 72;
   net->out_b = p; p += 1;
+}
+
+static void net_load(orc_net* net, const float* params, const float* buffers) {
+  net_load_frames(net, params, buffers, 3);
 }
 
 static void net_free(orc_net* net) {
@@ -570,10 +580,11 @@ static int forward_one(const orc_net* net, const float* in, int H, int W,
                        double* out, double* blocks) {
   if (H <= 0 || W <= 0 || H % 8 || W % 8) return -1;
   size_t n = (size_t)H * W;
-  double* x = malloc(sizeof(double) * 3 * n);
-  for (size_t t = 0; t < 3 * n; ++t) x[t] = (double)in[t];
+  const int T = net->frames;
+  double* x = malloc(sizeof(double) * T * n);
+  for (size_t t = 0; t < T * n; ++t) x[t] = (double)in[t];
   double* a = malloc(sizeof(double) * 8 * n);
-  orc_conv2d(x, 3, H, W, net->stem_w, NULL, 8, 3, 1, 1, 1, a);
+  orc_conv2d(x, T, H, W, net->stem_w, NULL, 8, 3, 1, 1, 1, a);
   batchnorm(a, 8, (int)n, net->stem_g, net->stem_b, net->stem_m, net->stem_v);
   relu(a, 8 * n);
   free(x);
@@ -616,6 +627,18 @@ int orc_forward(const float* params, const float* buffers, const float* in,
   orc_net net;
   net_load(&net, params, buffers);
   int rc = forward_one(&net, in, H, W, out, blocks);
+  net_free(&net);
+  return rc;
+}
+
+/* The fusion variants of Sec. IV-A: T = 2, 3 or 4 maps (frames t, t-1, ...)
+ * stacked as channels in place of three. */
+int orc_forward_frames(const float* params, const float* buffers, const float* in, int frames, int H, int W,
+                       double* out) {
+  if (frames < 1 || frames > 4) return -1;
+  orc_net net;
+  net_load_frames(&net, params, buffers, frames);
+  int rc = forward_one(&net, in, H, W, out, NULL);
   net_free(&net);
   return rc;
 }

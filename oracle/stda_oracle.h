@@ -97,6 +97,13 @@ int orc_num_buffers(void); /* BN running means and variances        */
 int orc_forward(const float* params, const float* buffers, const float* in,
                 int H, int W, double* out, double* blocks);
 
+/* The fusion variant with T (1..4) stacked maps in[T][H][W] (frames t,
+ * t-1, ...): the stem takes T input channels; params hold
+ * orc_num_params_frames(T) values in the canonical order. */
+int orc_num_params_frames(int frames);
+int orc_forward_frames(const float* params, const float* buffers, const float* in, int frames, int H, int W,
+                       double* out);
+
 /* Batch forward with nthreads POSIX threads; out[B][H][W]. */
 int orc_forward_batch(const float* params, const float* buffers,
                       const float* in, int B, int H, int W, double* out,

@@ -126,8 +126,12 @@ def _cout(b):
     return 2 * CIN[b] if ENC[b] else CIN[b] // 2
 
 
-def param_table():
-    """Canonical parameter tensors: list of (name, size, lo, hi)."""
+FRAMES = 3  # maps per window (Eq. concat_operation); the fusion variants take 2 or 4
+
+
+def param_table(frames: int = FRAMES):
+    """Canonical parameter tensors: list of (name, size, lo, hi). `frames`
+    input maps per window set the stem's input channels."""
     t = []
 
     def conv(name, size, fan):
@@ -138,7 +142,7 @@ def param_table():
         t.append((name + ".gamma", c, 0.8, 1.2))
         t.append((name + ".beta", c, -0.1, 0.1))
 
-    conv("stem.w", 216, 27)
+    conv("stem.w", 8 * frames * 9, frames * 9)
     bn("stem.bn", 8)
     for b in range(6):
         ci, co = CIN[b], _cout(b)
@@ -175,10 +179,11 @@ NUM_PARAMS = sum(s for _, s, _, _ in param_table())
 NUM_BUFFERS = 2 * sum(c for _, c in bn_table())
 
 
-def init_params(seed: int = 0):
-    """(params float32[NUM_PARAMS], buffers float32[NUM_BUFFERS]) from a seed."""
+def init_params(seed: int = 0, frames: int = FRAMES):
+    """(params float32[NUM_PARAMS], buffers float32[NUM_BUFFERS]) from a seed
+    (NUM_PARAMS of the 3-map network; the stem grows with `frames`)."""
     out = []
-    for tid, (name, size, lo, hi) in enumerate(param_table()):
+    for tid, (name, size, lo, hi) in enumerate(param_table(frames)):
         u = u01(key(seed, 0, 0, TAG_WEIGHT, tid, np.arange(size)))
         v = lo + (hi - lo) * u
         if name == "out.w":
@@ -193,10 +198,10 @@ def init_params(seed: int = 0):
     return params, np.concatenate(bufs)
 
 
-def param_offsets():
+def param_offsets(frames: int = FRAMES):
     """name -> (offset, size) in the flat parameter blob."""
     off, d = 0, {}
-    for name, size, _, _ in param_table():
+    for name, size, _, _ in param_table(frames):
         d[name] = (off, size)
         off += size
     return d

@@ -21,8 +21,9 @@ def torch_reference(params, buffers, x, requires_grad=False):
 
 
 def torch_forward(params, buffers, x, requires_grad=False):
+    frames = int(np.shape(x)[0])  # stacked maps (3 in the paper; 2 or 4 in the fusion variants)
     P = {k: torch.tensor(params[o:o + s].astype(np.float64), requires_grad=requires_grad)
-         for k, (o, s) in I.param_offsets().items()}
+         for k, (o, s) in I.param_offsets(frames).items()}
     bufs, off = {}, 0
     for name, c in I.bn_table():
         bufs[name] = (torch.tensor(buffers[off:off + c].astype(np.float64)),
@@ -35,7 +36,7 @@ def torch_forward(params, buffers, x, requires_grad=False):
 
     a = x if isinstance(x, torch.Tensor) else torch.tensor(np.asarray(x, np.float64))
     a = a[None]
-    a = F.relu(bn(F.conv2d(a, P["stem.w"].view(8, 3, 3, 3), padding=1), "stem.bn"))
+    a = F.relu(bn(F.conv2d(a, P["stem.w"].view(8, frames, 3, 3), padding=1), "stem.bn"))
     skips, blocks = [], []
     for b in range(6):
         ci, co, p = I.CIN[b], I._cout(b), f"blk{b}"
