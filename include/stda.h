@@ -81,6 +81,13 @@ typedef struct {
   stda_precision prec;
   uint64_t weight_seed;    /* random initialisation of the weights          */
   size_t mem_budget_bytes; /* serving admission limit; 0 = no limit         */
+  int frames;              /* maps stacked per window (Sec. IV-A, Eq.
+                              "concat_operation"): 3 as in the paper (0
+                              also means 3), or 2 / 4 for the fusion
+                              variants, which change only the stem's
+                              input channels. stda_backward, stda_submit and
+                              stda_forward_static need 3 (else
+                              STDA_ERR_UNSUPPORTED).                       */
 } stda_config;
 
 /* ---------------------------------------------------------------- context */
@@ -105,6 +112,13 @@ size_t stda_num_buffers(void);
 stda_status stda_init_params(uint64_t seed, float* host_params,
                              float* host_buffers);
 
+/* The same for a context of `frames` (1..4) stacked maps: the stem weight
+ * is W[8][frames][3][3], so the parameter count is 137915 + 72 (frames - 3);
+ * every other tensor has the same values as for three maps. */
+size_t stda_num_params_frames(int frames);
+stda_status stda_init_params_frames(uint64_t seed, int frames, float* host_params,
+                                    float* host_buffers);
+
 /* Structural re-parameterisation for deployment (host only, no GPU). The
  * paper's blocks train as multi-branch MobileOne-style units (Sec. IV-B,
  * Eqs. "mobile_encoder_stage1/2", "mobile_decoder_stage1/2": dw 1x1 + BN,
@@ -112,7 +126,7 @@ stda_status stda_init_params(uint64_t seed, float* host_params,
  * branch) and collapse at inference into one conv + bias per branch. This
  * writes that inference network, with every BN folded in FP64 and rounded
  * to float once, in PyTorch weight layouts, concatenated in this order:
- *   stem.weight [8][3][3][3], stem.bias [8]      Conv2d(3, 8, 3, padding 1) + ReLU
+ *   stem.weight [8][T][3][3], stem.bias [8]      Conv2d(T, 8, 3, padding 1) + ReLU
  *   for each block b = 0..5 (Cin 8,16,32,64,32,16; Cout 16,32,64,32,16,8):
  *     dw.weight [Cin][1][3][3], dw.bias [Cin]    depthwise Conv2d(padding 1,
  *                                                groups Cin) + ReLU (the
@@ -129,11 +143,12 @@ stda_status stda_init_params(uint64_t seed, float* host_params,
  *                                                sigmoid, scales y
  *   out.weight [1][8][3][3], out.bias [1]        Conv2d(8, 1, 3, padding 1) + sigmoid
  * with the skips D1 += E2 (input of block 4) and D2 += E1 (input of block 5)
- * after ECA. host_params / host_buffers as for stda_init_params; host_out
- * holds n = stda_reparam_count() floats. Returns STDA_ERR_INVALID_ARG on a null
- * pointer or a wrong n. */
-size_t stda_reparam_count(void);
-stda_status stda_reparam_export(const float* host_params, const float* host_buffers,
+ * after ECA; T = frames stacked maps (1..4; 3 in the paper). host_params /
+ * host_buffers as for stda_init_params_frames; host_out holds
+ * n = stda_reparam_count(frames) floats. Returns STDA_ERR_INVALID_ARG on a
+ * null pointer, frames outside 1..4 or a wrong n. */
+size_t stda_reparam_count(int frames);
+stda_status stda_reparam_export(const float* host_params, const float* host_buffers, int frames,
                                 float* host_out, size_t n);
 
 /* Copies the FP32 parameters / BN buffers to or from host memory (n must
@@ -146,7 +161,7 @@ stda_status stda_set_buffers(stda_ctx* ctx, const float* host_src, size_t n);
 
 /* ---------------------------------------------------------------- forward */
 
-/* Denoises B windows: d_in [B][3][H][W] -> d_out [B][1][H][W] (Sec. IV-A,
+/* Denoises B windows: d_in [B][frames][H][W] -> d_out [B][1][H][W] (Sec. IV-A,
  * Eqs. "encoder_stda", "decoder_stda"). H, W may be smaller than the
  * context's, but B*H*W may not exceed max_batch*H_ctx*W_ctx. B == 0 is a
  * no-op. */

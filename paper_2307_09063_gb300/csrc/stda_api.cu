@@ -52,7 +52,7 @@ struct Tensor {
   bool out_w;
 };
 
-std::vector<Tensor> param_table() {
+std::vector<Tensor> param_table(int frames) {
   std::vector<Tensor> t;
   auto conv = [&](int size, int fan) {
     double b = std::sqrt(6.0 / fan);
@@ -62,7 +62,7 @@ std::vector<Tensor> param_table() {
     t.push_back({c, 0.8, 1.2, false});
     t.push_back({c, -0.1, 0.1, false});
   };
-  conv(216, 27);
+  conv(8 * frames * 9, frames * 9);
   bn(8);
   for (int b = 0; b < kNumBlocks; ++b) {
     int ci = kBlkCin[b], co = kBlkCout[b];
@@ -98,8 +98,14 @@ std::vector<int> bn_channels() {
 
 }  // namespace
 
-void init_params(uint64_t seed, float* params, float* buffers) {
-  auto tab = param_table();
+size_t num_params(int frames) {
+  size_t n = 0;
+  for (const Tensor& t : param_table(frames)) n += t.size;
+  return n;
+}
+
+void init_params(uint64_t seed, float* params, float* buffers, int frames) {
+  auto tab = param_table(frames);
   size_t off = 0;
   for (size_t tid = 0; tid < tab.size(); ++tid) {
     const Tensor& t = tab[tid];
@@ -127,7 +133,7 @@ void init_params(uint64_t seed, float* params, float* buffers) {
 // s1 * w1 + s3, bias t1 + t2 + t3. The decoder's stride-1 transposed 3x3 is
 // the cross-correlation with the kernel flipped in both axes.
 // ----------------------------------------------------------------------------
-FoldedOffsets folded_layout() {
+FoldedOffsets folded_layout(int frames) {
   FoldedOffsets o;
   size_t p = 0;
   auto take = [&](size_t n) {
@@ -135,7 +141,7 @@ FoldedOffsets folded_layout() {
     p += (n + 63) / 64 * 64;
     return r;
   };
-  o.stem_w = take(27 * 8);
+  o.stem_w = take(frames * 9 * 8);
   o.stem_b = take(8);
   for (int b = 0; b < kNumBlocks; ++b) {
     int ci = kBlkCin[b], co = kBlkCout[b];
@@ -180,19 +186,20 @@ BnFold bn_fold(const std::vector<double>& g, const std::vector<double>& be, cons
 }
 }  // namespace
 
-void fold_params(const float* params, const float* buffers, float* dst, FoldedOffsets* off) {
-  *off = folded_layout();
+void fold_params(const float* params, const float* buffers, float* dst, FoldedOffsets* off, int frames) {
+  *off = folded_layout(frames);
   std::memset(dst, 0, sizeof(float) * off->total);
   Cursor c{params};
   const float* bq = buffers;
   {
-    auto w = c.take(216);
+    auto w = c.take(8 * frames * 9);
     auto g = c.take(8);
     auto be = c.take(8);
     BnFold f = bn_fold(g, be, bq, 8);
     for (int o = 0; o < 8; ++o)
-      for (int ci = 0; ci < 3; ++ci)
-        for (int t = 0; t < 9; ++t) dst[off->stem_w + (ci * 9 + t) * 8 + o] = (float)(w[(o * 3 + ci) * 9 + t] * f.s[o]);
+      for (int ci = 0; ci < frames; ++ci)
+        for (int t = 0; t < 9; ++t)
+          dst[off->stem_w + (ci * 9 + t) * 8 + o] = (float)(w[(o * frames + ci) * 9 + t] * f.s[o]);
     for (int o = 0; o < 8; ++o) dst[off->stem_b + o] = (float)f.t[o];
   }
   for (int b = 0; b < kNumBlocks; ++b) {
@@ -259,8 +266,8 @@ void fold_params(const float* params, const float* buffers, float* dst, FoldedOf
 
 // Inference network in PyTorch weight layouts (the order documented with
 // stda_reparam_export), BN folded in FP64 exactly as fold_params does.
-size_t reparam_count() {
-  size_t n = 216 + 8 + 72 + 1;
+size_t reparam_count(int frames) {
+  size_t n = 8 * frames * 9 + 8 + 72 + 1;
   for (int b = 0; b < kNumBlocks; ++b) {
     const size_t ci = kBlkCin[b], co = kBlkCout[b], dense = (kBlkEnc[b] ? 9 : 16) * ci * co;
     n += 9 * ci + ci + 2 * dense + 2 * co + 3;
@@ -268,17 +275,17 @@ size_t reparam_count() {
   return n;
 }
 
-void reparam_export(const float* params, const float* buffers, float* out) {
+void reparam_export(const float* params, const float* buffers, int frames, float* out) {
   Cursor c{params};
   const float* bq = buffers;
   float* o = out;
   {
-    auto w = c.take(216);
+    auto w = c.take(8 * frames * 9);
     auto g = c.take(8);
     auto be = c.take(8);
     BnFold f = bn_fold(g, be, bq, 8);
     for (int oc = 0; oc < 8; ++oc)
-      for (int k = 0; k < 27; ++k) *o++ = (float)(w[oc * 27 + k] * f.s[oc]);
+      for (int k = 0; k < frames * 9; ++k) *o++ = (float)(w[oc * frames * 9 + k] * f.s[oc]);
     for (int oc = 0; oc < 8; ++oc) *o++ = (float)f.t[oc];
   }
   for (int b = 0; b < kNumBlocks; ++b) {
@@ -323,8 +330,9 @@ void reparam_export(const float* params, const float* buffers, float* out) {
 
 const char* const kKernelNames[K_NUM_IDS] = {"enc1_stem", "enc2", "enc3", "dec1", "dec2", "dec3", "out"};
 
-NetW net_from(const float* base, const FoldedOffsets& o) {
+NetW net_from(const float* base, const FoldedOffsets& o, int frames) {
   NetW n;
+  n.frames = frames;
   n.stem_w = base + o.stem_w;
   n.stem_b = base + o.stem_b;
   for (int b = 0; b < kNumBlocks; ++b)
@@ -389,6 +397,7 @@ struct Profiler : stda::KernelHook {
 struct stda_ctx {
   Profiler prof;
   stda_config cfg;
+  int frames = 3;  // stacked maps per window
   int device = 0;
   std::vector<float> params, buffers;
   stda::FoldedOffsets off;
@@ -427,11 +436,11 @@ stda_status cuda_fail(stda_ctx* c, cudaError_t e, const char* where) {
 size_t elem_size(stda_precision p) { return p == STDA_FP32 ? 4 : 2; }
 
 stda_status upload_weights(stda_ctx* c) {
-  std::vector<float> host(stda::folded_layout().total);
-  stda::fold_params(c->params.data(), c->buffers.data(), host.data(), &c->off);
+  std::vector<float> host(stda::folded_layout(c->frames).total);
+  stda::fold_params(c->params.data(), c->buffers.data(), host.data(), &c->off, c->frames);
   cudaError_t e = cudaMemcpy(c->d_folded, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e) return cuda_fail(c, e, "upload weights");
-  c->net = stda::net_from(c->d_folded, c->off);
+  c->net = stda::net_from(c->d_folded, c->off, c->frames);
   std::vector<unsigned char> blob;
   // FP8: E4M3 stage-2 operands in every block but the first (8 input channels)
   bool f8[6];
@@ -449,6 +458,7 @@ stda_status upload_weights(stda_ctx* c) {
   if ((e = cudaMemcpy(c->d_tc, blob.data(), blob.size(), cudaMemcpyHostToDevice)))
     return cuda_fail(c, e, "upload tc weights");
   c->tcw = stda::tc_weights_from(c->d_tc, c->tc_off);
+  if (c->frames != 3) return STDA_OK;  // the training graph is the three-map network
   if (!c->d_canon &&
       (e = cudaMalloc((void**)&c->d_canon, sizeof(float) * (stda::kNumParams + stda::kNumBuffers))))
     return cuda_fail(c, e, "alloc canonical parameters");
@@ -490,15 +500,18 @@ stda_status stda_create(const stda_config* cfg, stda_ctx** out) {
   if (cfg->prec != STDA_FP32 && cfg->prec != STDA_BF16 && cfg->prec != STDA_FP8_E4M3 &&
       cfg->prec != STDA_FP8_E4M3_FAST)
     return STDA_ERR_INVALID_ARG;
+  const int frames = cfg->frames == 0 ? 3 : cfg->frames;
+  if (frames < 1 || frames > stda::kMaxFrames) return STDA_ERR_INVALID_ARG;
   stda_ctx* c = new stda_ctx;
   c->cfg = *cfg;
+  c->frames = frames;
   cudaGetDevice(&c->device);
   const char* fs = getenv("STDA_FORCE_SIMT");
   c->force_simt = fs && fs[0] == '1';
-  c->params.resize(stda::kNumParams);
+  c->params.resize(stda::num_params(frames));
   c->buffers.resize(stda::kNumBuffers);
-  stda::init_params(cfg->weight_seed, c->params.data(), c->buffers.data());
-  if (cudaMalloc((void**)&c->d_folded, stda::folded_layout().total * sizeof(float))) {
+  stda::init_params(cfg->weight_seed, c->params.data(), c->buffers.data(), frames);
+  if (cudaMalloc((void**)&c->d_folded, stda::folded_layout(frames).total * sizeof(float))) {
     cudaGetLastError();
     stda_destroy(c);
     return STDA_ERR_OOM;
@@ -544,11 +557,24 @@ stda_status stda_init_params(uint64_t seed, float* params, float* buffers) {
   return STDA_OK;
 }
 
-size_t stda_reparam_count(void) { return stda::reparam_count(); }
+size_t stda_reparam_count(int frames) {
+  return frames >= 1 && frames <= stda::kMaxFrames ? stda::reparam_count(frames) : 0;
+}
 
-stda_status stda_reparam_export(const float* params, const float* buffers, float* out, size_t n) {
-  if (!params || !buffers || !out || n != stda::reparam_count()) return STDA_ERR_INVALID_ARG;
-  stda::reparam_export(params, buffers, out);
+stda_status stda_reparam_export(const float* params, const float* buffers, int frames, float* out, size_t n) {
+  if (!params || !buffers || !out || frames < 1 || frames > stda::kMaxFrames || n != stda::reparam_count(frames))
+    return STDA_ERR_INVALID_ARG;
+  stda::reparam_export(params, buffers, frames, out);
+  return STDA_OK;
+}
+
+size_t stda_num_params_frames(int frames) {
+  return frames >= 1 && frames <= stda::kMaxFrames ? stda::num_params(frames) : 0;
+}
+
+stda_status stda_init_params_frames(uint64_t seed, int frames, float* params, float* buffers) {
+  if (!params || !buffers || frames < 1 || frames > stda::kMaxFrames) return STDA_ERR_INVALID_ARG;
+  stda::init_params(seed, params, buffers, frames);
   return STDA_OK;
 }
 
@@ -627,6 +653,7 @@ __global__ void k_bf16_to_f32_flat(const __nv_bfloat16* a, float* o, long n) {
 stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, const float* d_gout,
                           float* d_gparams, double* d_loss, float* d_gin, float* d_out, int B, int H, int W,
                           cudaStream_t st) {
+  if (c && c->frames != 3) return fail(c, STDA_ERR_UNSUPPORTED, "backward: the training step takes three maps");
   if (!c) return STDA_ERR_INVALID_ARG;
   if (B < 0 || B > c->cfg.max_batch) return fail(c, STDA_ERR_SHAPE, "backward: batch out of range");
   if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "backward: H and W must be positive multiples of 8");
@@ -674,6 +701,7 @@ stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, c
 
 stda_status stda_submit(stda_ctx* c, int radar, int H, int W, const void* d_frame, void* d_out, cudaEvent_t done,
                         cudaStream_t st) {
+  if (c && c->frames != 3) return fail(c, STDA_ERR_UNSUPPORTED, "submit: serving takes three maps per window");
   if (!c) return STDA_ERR_INVALID_ARG;
   if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "submit: H and W must be positive multiples of 8");
   if (!d_frame || !d_out) return fail(c, STDA_ERR_INVALID_ARG, "submit: null pointer");

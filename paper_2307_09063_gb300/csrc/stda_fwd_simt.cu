@@ -94,7 +94,7 @@ struct EncSmem {
   static constexpr int R1 = 2 * TY + 1, C1 = 2 * TX + 1;
   static constexpr int RI = R0 + 2, CIW = C0 + 2;
   static constexpr int CO = 2 * CI;
-  static constexpr int n_in = STEM ? 3 * RI * CIW : 0;
+  static constexpr int n_in = STEM ? kMaxFrames * RI * CIW : 0;  // up to kMaxFrames maps
   static constexpr int n_x0 = R0 * C0 * CIP;
   static constexpr int n_x1 = R1 * C1 * CIP;
   static constexpr int n_o = TY * TX * CO;
@@ -124,14 +124,15 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
   const BlockW bw = a.w.blk[a.blk];
 
   if (STEM) {
-    const T* in = a.in + (size_t)b * 3 * H * W;
-    for (int i = threadIdx.x; i < S::n_in; i += blockDim.x) {
+    const int NF = a.w.frames;
+    const T* in = a.in + (size_t)b * NF * H * W;
+    for (int i = threadIdx.x; i < NF * S::RI * S::CIW; i += blockDim.x) {
       int c = i / (S::RI * S::CIW), r = (i / S::CIW) % S::RI, q = i % S::CIW;
       int y = y0 - 1 + r, x = x0c - 1 + q;
       s_in[i] = (y >= 0 && y < H && x >= 0 && x < W) ? tof(in[((size_t)c * H + y) * W + x]) : 0.f;
     }
     __syncthreads();
-    // stem: conv3x3 3 -> 8 (BN folded) + ReLU; zero outside the map (padding)
+    // stem: conv3x3 frames -> 8 (BN folded) + ReLU; zero outside the map (padding)
     for (int i = threadIdx.x; i < S::R0 * S::C0; i += blockDim.x) {
       int r = i / S::C0, q = i % S::C0, y = y0 + r, x = x0c + q;
       float acc[8];
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
       for (int o = 0; o < 8; ++o) acc[o] = a.w.stem_b[o];
       bool inside = (y >= 0 && y < H && x >= 0 && x < W);
       if (inside) {
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < NF; ++c)
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
             float v = s_in[(c * S::RI + r + t / 3) * S::CIW + q + t % 3];

@@ -300,7 +300,7 @@ __host__ __device__ constexpr bool dec_stacked(int ci) { return ci <= 32; }
 // (group g, slot s at 2 g + s) and the TMEM address slot first, then the MMA
 // descriptor table (two accumulators x phases x K-steps), ECA g / s of the
 // input (2 Cin) and of the skip (Cin), stage-1 weights and bias (10 Cin),
-// stem weights and bias (224, stem block only), per-warp channel sums (up to
+// stem weights and bias (72 per stacked map + 8, stem block only), per-warp channel sums (up to
 // 16 warps x Cout, also the ECA reduction scratch of up to 512 threads),
 // and the epilogue constants: BN shift and residual bias (Cout each) and the
 // E4M3 weight scales of the two branches (one per TMEM column of a branch).
@@ -328,7 +328,7 @@ __host__ __device__ constexpr MiscLayout misc_layout(int CI, bool enc, bool f8) 
   m.g = misc_take(off, 4 * 2 * CI);
   m.ss = misc_take(off, 4 * CI);
   m.dw = misc_take(off, 4 * 10 * CI);
-  m.stem = misc_take(off, enc && CI == 8 ? 4 * 224 : 0);
+  m.stem = misc_take(off, enc && CI == 8 ? 4 * (72 * kMaxFrames + 8) : 0);
   m.red = misc_take(off, 4 * red);
   m.b2 = misc_take(off, 4 * CO);
   m.rb = misc_take(off, 4 * CO);
@@ -375,7 +375,7 @@ struct Misc {
     dw = (float*)(p + l.dw);
     dwb = dw + 9 * CI;
     stw = (float*)(p + l.stem);
-    stb = stw + 216;
+    stb = stw + 72 * kMaxFrames;
     red = (float*)(p + l.red);
     b2 = (float*)(p + l.b2);
     rb = (float*)(p + l.rb);
@@ -481,14 +481,14 @@ __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32
 }
 
 // ---------------------------------------------------------------- encoder
-template <int CI, bool STEM, bool F8>
+template <int CI, bool STEM, bool F8, int NF = 3>
 __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   using OP = Op<F8>;
   constexpr int CG = OP::CG, G = CI / CG, CO = 2 * CI, NP = CO;
   static_assert(!(STEM && F8), "the stem block runs in bf16");
   extern __shared__ __align__(1024) unsigned char sm[];
   const int nsteps = a.nsteps, T = a.L.terms;
-  const int in_bytes = STEM ? 3 * (2 * a.band + 6) * (a.w + 16) * 2 : 0;
+  const int in_bytes = STEM ? NF * (2 * a.band + 6) * (a.w + 16) * 2 : 0;
   constexpr MiscLayout ML = misc_layout(CI, true, F8);
   const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes, T, ML.total);
   const size_t lo_off = (size_t)4 * G * a.PIXA * 16;  // low-term planes follow the high-term ones
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
     M.sr[i] = F8 ? a.L.swr[i] : 1.f;
   }
   if (STEM) {
-    for (int i = tid; i < 216; i += blockDim.x) M.stw[i] = a.stem_w[i];
+    for (int i = tid; i < 72 * NF; i += blockDim.x) M.stw[i] = a.stem_w[i];
     for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
   }
   if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
@@ -554,9 +554,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   if (STEM) {
     const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy0 - 3, nch = CW / 8;
     __nv_bfloat16* sin = (__nv_bfloat16*)(sm + L.off_in);
-    const __nv_bfloat16* in = a.in + (size_t)b * 3 * h * w;
+    const __nv_bfloat16* in = a.in + (size_t)b * NF * h * w;
     batched<8>(
-        3 * RI * nch,
+        NF * RI * nch,
         [&](int i) {
           int c = i / (RI * nch), r = (i / nch) % RI, x = (i % nch) * 8 - 8, y = yi0 + r;
           return (y >= 0 && y < h && x >= 0 && x < w) ? *(const uint4*)(in + ((size_t)c * h + y) * w + x)
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
         },
         [&](int i, uint4 v) { *(uint4*)(sin + (size_t)i * 8) = v; });
     __syncthreads();
-    // stem conv 3 -> 8: four horizontally adjacent positions per thread share
+    // stem conv NF -> 8: four horizontally adjacent positions per thread share
     // the weight loads; channel pairs go through packed FP32 FMAs
     const int w4 = w / 4;
     for (int i = tid; i < (y_hi - y_lo + 1) * w4; i += blockDim.x) {
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[p][k] = make_float2(M.stb[2 * k], M.stb[2 * k + 1]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < NF; ++c)
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
           // columns x - 1 .. x + 4 sit at row[x + 7 .. x + 12]: one 4-, one
@@ -1024,7 +1024,7 @@ int plane_skew(int touched) { return touched >= 8 ? 1 : 8 / touched; }
 // rows for the decoder) and CTA shape (pass 0: two CTAs of 256 threads per
 // SM, shared memory <= half, TMEM <= 256 columns; pass 1: one CTA of 512
 // threads). band = 0 if it does not fit.
-Geo encoder_geo_at(int b, bool f8, int terms, int w, int TY, int pass) {
+Geo encoder_geo_at(int b, bool f8, int terms, int w, int TY, int pass, int frames) {
   const int CI = kBlkCin[b], CO = 2 * CI, G = CI / (f8 ? 16 : 8), wo = w / 2, nsteps = steps_per_acc(b, f8);
   const bool stem = b == 0;
   Geo g{};
@@ -1034,7 +1034,7 @@ Geo encoder_geo_at(int b, bool f8, int terms, int w, int TY, int pass) {
   g.ntile = cdiv(count, 128);
   g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
   g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-  const int in_bytes = stem ? 3 * (2 * TY + 6) * (w + 16) * 2 : 0;
+  const int in_bytes = stem ? frames * (2 * TY + 6) * (w + 16) * 2 : 0;
   g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms, misc_layout(CI, true, f8).total).total;
   g.threads = pass == 0 ? 256 : 512;
   pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
@@ -1061,9 +1061,10 @@ Geo decoder_geo_at(int b, bool f8, int terms, int w, int TA, int pass) {
   return g;
 }
 
-Geo level_geo(int b, bool f8, int terms, int h, int w) {
+Geo level_geo(int b, bool f8, int terms, int h, int w, int frames) {
   auto at = [&](int TA, int pass) {
-    return kBlkEnc[b] ? encoder_geo_at(b, f8, terms, w, TA, pass) : decoder_geo_at(b, f8, terms, w, TA, pass);
+    return kBlkEnc[b] ? encoder_geo_at(b, f8, terms, w, TA, pass, frames)
+                      : decoder_geo_at(b, f8, terms, w, TA, pass);
   };
   if (const int TA = band_override(b)) {
     for (int pass = 0; pass < 2; ++pass) {
@@ -1291,7 +1292,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     const int h = H / in_div[l], wd = W / in_div[l];
     const bool f8 = tw.layer[l].f8;
     const int terms = tw.layer[l].terms;
-    Geo g = level_geo(l, f8, terms, h, wd);
+    Geo g = level_geo(l, f8, terms, h, wd, w.frames);
     if (g.band == 0) return cudaErrorInvalidConfiguration;
     TcArgs a{};
     a.in = (const __nv_bfloat16*)(l == 0 ? (const void*)in : prev);
@@ -1334,7 +1335,12 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     tiles[l] = a.tiles_per_window;
     hook->begin(K_ENC1 + l, st);
     switch (l * 2 + (f8 ? 1 : 0)) {
-      case 0: e = launch(k_enc_tc<8, true, false>, g, B, a, st); break;
+      case 0:
+        e = w.frames == 2   ? launch(k_enc_tc<8, true, false, 2>, g, B, a, st)
+            : w.frames == 4 ? launch(k_enc_tc<8, true, false, 4>, g, B, a, st)
+            : w.frames == 3 ? launch(k_enc_tc<8, true, false, 3>, g, B, a, st)
+                            : cudaErrorInvalidValue;
+        break;
       case 2: e = launch(k_enc_tc<16, false, false>, g, B, a, st); break;
       case 3: e = launch(k_enc_tc<16, false, true>, g, B, a, st); break;
       case 4: e = launch(k_enc_tc<32, false, false>, g, B, a, st); break;

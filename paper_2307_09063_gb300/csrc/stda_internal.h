@@ -34,8 +34,11 @@ struct BlockW {
   const float *dw, *dwb, *w2, *b2, *rw, *rb, *eca;
 };
 
+constexpr int kMaxFrames = 4;  // stacked maps per window (3 in the paper)
+
 struct NetW {
-  const float* stem_w;  // [27 = ci*9 + tap][8]
+  int frames;           // stacked input maps = stem input channels
+  const float* stem_w;  // [frames * 9 = ci*9 + tap][8]
   const float* stem_b;  // [8]
   BlockW blk[6];
   const float* out_w;  // [9 taps][8]
@@ -50,12 +53,13 @@ struct FoldedOffsets {
   size_t total;
 };
 void fold_params(const float* params, const float* buffers, float* dst,
-                 FoldedOffsets* off);
-FoldedOffsets folded_layout();
-NetW net_from(const float* dev_base, const FoldedOffsets& off);
+                 FoldedOffsets* off, int frames = 3);
+FoldedOffsets folded_layout(int frames = 3);
+NetW net_from(const float* dev_base, const FoldedOffsets& off, int frames = 3);
 
 // Parameter initialisation from a seed (SplitMix64 uniform draws).
-void init_params(uint64_t seed, float* params, float* buffers);
+size_t num_params(int frames);
+void init_params(uint64_t seed, float* params, float* buffers, int frames = 3);
 
 // Activation scratch of one forward pass for B windows of H x W.
 struct FwdScratch {

@@ -28,7 +28,7 @@ class StdaError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("max_batch", ctypes.c_int), ("prec", ctypes.c_int),
-                ("weight_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_size_t)]
+                ("weight_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_size_t), ("frames", ctypes.c_int)]
 
 
 class GenConfig(ctypes.Structure):
@@ -61,7 +61,11 @@ def lib():
             getattr(L, n).argtypes = [_VP, _VP, ctypes.c_size_t]
         L.stda_init_params.argtypes = [ctypes.c_uint64, _VP, _VP]
         L.stda_reparam_count.restype = ctypes.c_size_t
-        L.stda_reparam_export.argtypes = [_VP, _VP, _VP, ctypes.c_size_t]
+        L.stda_reparam_count.argtypes = [ctypes.c_int]
+        L.stda_reparam_export.argtypes = [_VP, _VP, ctypes.c_int, _VP, ctypes.c_size_t]
+        L.stda_num_params_frames.restype = ctypes.c_size_t
+        L.stda_num_params_frames.argtypes = [ctypes.c_int]
+        L.stda_init_params_frames.argtypes = [ctypes.c_uint64, ctypes.c_int, _VP, _VP]
         L.stda_forward.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_device_status.argtypes = [_VP]
         L.stda_last_error.restype = ctypes.c_char_p
@@ -109,22 +113,23 @@ def num_buffers():
     return int(lib().stda_num_buffers())
 
 
-def init_params(seed=0):
-    """Host-side: the parameters and BN buffers stda_create draws from a seed."""
-    p = np.empty(num_params(), np.float32)
+def init_params(seed=0, frames=3):
+    """Host-side: the parameters and BN buffers stda_create draws from a seed
+    for a context of `frames` stacked maps per window."""
+    p = np.empty(int(lib().stda_num_params_frames(frames)), np.float32)
     b = np.empty(num_buffers(), np.float32)
-    st = lib().stda_init_params(seed, p.ctypes.data, b.ctypes.data)
+    st = lib().stda_init_params_frames(seed, frames, p.ctypes.data, b.ctypes.data)
     if st != OK:
         raise StdaError(st)
     return p, b
 
 
-def reparam_shapes():
+def reparam_shapes(frames=3):
     """(name, shape) of the re-parameterised inference network, in the order
     of stda_reparam_export (PyTorch Conv2d / ConvTranspose2d / Conv1d
     weight layouts)."""
     cin, enc = (8, 16, 32, 64, 32, 16), (1, 1, 1, 0, 0, 0)
-    t = [("stem.weight", (8, 3, 3, 3)), ("stem.bias", (8,))]
+    t = [("stem.weight", (8, frames, 3, 3)), ("stem.bias", (8,))]
     for b in range(6):
         ci = cin[b]
         co = 2 * ci if enc[b] else ci // 2
@@ -136,19 +141,19 @@ def reparam_shapes():
     return t + [("out.weight", (1, 8, 3, 3)), ("out.bias", (1,))]
 
 
-def reparam_export(params, buffers):
+def reparam_export(params, buffers, frames=3):
     """Host-side: the re-parameterised inference network (every BN folded,
     stage-1 branches merged) as {name: float32 array}, through
     stda_reparam_export."""
-    n = int(lib().stda_reparam_count())
+    n = int(lib().stda_reparam_count(frames))
     out = np.empty(n, np.float32)
     p = np.ascontiguousarray(params, np.float32)
     b = np.ascontiguousarray(buffers, np.float32)
-    st = lib().stda_reparam_export(p.ctypes.data, b.ctypes.data, out.ctypes.data, n)
+    st = lib().stda_reparam_export(p.ctypes.data, b.ctypes.data, frames, out.ctypes.data, n)
     if st != OK:
         raise StdaError(st)
     d, off = {}, 0
-    for name, shape in reparam_shapes():
+    for name, shape in reparam_shapes(frames):
         k = int(np.prod(shape))
         d[name] = out[off:off + k].reshape(shape)
         off += k
@@ -160,11 +165,11 @@ class Context:
     """One libstda context: folded weights and activation scratch on the
     current CUDA device for up to max_batch windows of H x W."""
 
-    def __init__(self, H, W, max_batch, precision="fp32", weight_seed=0, mem_budget_bytes=0):
+    def __init__(self, H, W, max_batch, precision="fp32", weight_seed=0, mem_budget_bytes=0, frames=3):
         self.precision = precision
         self.prec = PRECISIONS[precision]
-        self.H, self.W, self.max_batch = H, W, max_batch
-        cfg = Config(H, W, max_batch, self.prec, weight_seed, mem_budget_bytes)
+        self.H, self.W, self.max_batch, self.frames = H, W, max_batch, frames
+        cfg = Config(H, W, max_batch, self.prec, weight_seed, mem_budget_bytes, frames)
         h = _VP()
         st = lib().stda_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:
@@ -193,7 +198,7 @@ class Context:
             raise StdaError(st, lib().stda_last_error(self.h).decode())
 
     def get_params(self):
-        a = np.empty(num_params(), np.float32)
+        a = np.empty(int(lib().stda_num_params_frames(self.frames)), np.float32)
         self._check(lib().stda_get_params(self.h, a.ctypes.data, a.size))
         return a
 
@@ -215,10 +220,10 @@ class Context:
         return lib().stda_forward(self.h, _ptr(x), _ptr(out), B, H, W, _stream(stream))
 
     def forward(self, x, out=None, stream=None):
-        """x: CUDA tensor [B][3][H][W] (float32 for fp32, bfloat16 otherwise)."""
+        """x: CUDA tensor [B][frames][H][W] (float32 for fp32, bfloat16 otherwise)."""
         import torch
 
-        assert x.is_cuda and x.is_contiguous() and x.dtype == self.io_dtype and x.dim() == 4 and x.shape[1] == 3
+        assert x.is_cuda and x.is_contiguous() and x.dtype == self.io_dtype and x.dim() == 4 and x.shape[1] == self.frames
         B, _, H, W = x.shape
         if out is None:
             out = torch.empty((B, 1, H, W), dtype=x.dtype, device=x.device)

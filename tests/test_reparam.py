@@ -13,7 +13,7 @@ from paper_2307_09063_gb300 import inputs as I
 from paper_2307_09063_gb300 import stda as S
 
 
-def folded_forward(net, x):
+def folded_forward(net, x):  # x [frames][H][W]
     """The inference network of the export, from PyTorch float64 operators."""
     t = {k: torch.tensor(v.astype(np.float64)) for k, v in net.items()}
     a = torch.tensor(np.asarray(x, np.float64))[None]
@@ -40,7 +40,8 @@ def folded_forward(net, x):
 
 def test_count_and_shapes():
     n = sum(int(np.prod(s)) for _, s in S.reparam_shapes())
-    assert n == S.lib().stda_reparam_count() == 136731
+    assert n == S.lib().stda_reparam_count(3) == 136731
+    assert S.lib().stda_reparam_count(4) == n + 72 and S.lib().stda_reparam_count(5) == 0
     params, bufs = I.init_params(0)
     net = S.reparam_export(params, bufs)
     assert all(np.all(np.isfinite(v)) for v in net.values())
@@ -93,4 +94,23 @@ def test_identity_bn_exposes_the_raw_branches():
 def test_bad_arguments():
     params, bufs = I.init_params(0)
     out = np.empty(10, np.float32)
-    assert S.lib().stda_reparam_export(params.ctypes.data, bufs.ctypes.data, out.ctypes.data, 10) == S.ERR_INVALID_ARG
+    assert S.lib().stda_reparam_export(params.ctypes.data, bufs.ctypes.data, 3, out.ctypes.data, 10) == S.ERR_INVALID_ARG
+    n = S.lib().stda_reparam_count(3)
+    big = np.empty(n, np.float32)
+    assert S.lib().stda_reparam_export(params.ctypes.data, bufs.ctypes.data, 0, big.ctypes.data, n) == S.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("T", [2, 4])
+def test_folded_fusion_variant_matches_oracle(T):
+    params, bufs = I.init_params(4, frames=T)
+    net = S.reparam_export(params, bufs, frames=T)
+    assert net["stem.weight"].shape == (8, T, 3, 3)
+    x = np.random.default_rng(T).uniform(0, 1, (T, 16, 24))
+    assert np.max(np.abs(folded_forward(net, x) - O.forward_frames(params, bufs, x))) <= 2e-6
+
+
+def test_library_init_params_frames_bit_exact():
+    for T in (2, 3, 4):
+        p, b = S.init_params(9, frames=T)
+        pr, br = I.init_params(9, frames=T)
+        assert np.array_equal(p, pr) and np.array_equal(b, br)
