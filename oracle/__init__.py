@@ -249,6 +249,23 @@ def forward_batch(params, buffers, x, nthreads=None):
     return out
 
 
+def loss_grad_bn(params, buffers, x, target, mode=1):
+    """MSE loss, dL/dtheta [num_params] and the BN statistics used
+    ([num_buffers], BN-buffer layout) of a batch x[B][3][H][W] against
+    target[B][H][W], with BN in training mode (mode 1: batch statistics) or
+    with the running statistics (mode 0)."""
+    params, buffers, x, target = _f32(params), _f32(buffers), _f32(x), _f32(target)
+    B, _, H, W = x.shape
+    g = np.empty(num_params())
+    st = np.empty(num_buffers())
+    lib().orc_loss_grad_bn.restype = ctypes.c_double
+    loss = lib().orc_loss_grad_bn(_p(params, _F), _p(buffers, _F), _p(x, _F), _p(target, _F), B, H, W, mode,
+                                  _p(g, _D), _p(st, _D))
+    if np.isnan(loss):
+        raise ValueError(f"oracle rejected shape {H}x{W}")
+    return loss, g, st
+
+
 def conv2d(x, w, bias, stride, pad, groups):
     x, w = _f64(x), _f64(w)
     Ci, H, W = x.shape

@@ -1089,6 +1089,368 @@ double orc_loss_grad(const float* params, const float* buffers, const float* in,
 }
 
 /* ======================================================================== */
+/* Training-mode BatchNorm (batch statistics), FP64.                        */
+/* ======================================================================== */
+
+/* In training mode a BN normalises with the mean and the biased variance of
+ * its input over the whole batch (every window and pixel of a channel), so
+ * each window's forward pass and adjoint depend on all the others. The
+ * batch network below holds every layer's tensors for all B windows
+ * ([B][C][n]) and takes the convolutions window by window with the
+ * primitives above. mode 0 normalises with the running statistics instead
+ * and then computes the same loss and gradient as orc_loss_grad. */
+
+/* Per-channel mean and biased variance of x[B][C][n] (two passes). */
+static void bnb_stats(const double* x, int B, int C, size_t n, double* mean, double* var) {
+  double N = (double)B * (double)n;
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b)
+      for (size_t t = 0; t < n; ++t) s += x[((size_t)b * C + c) * n + t];
+    double m = s / N, q = 0.0;
+    for (int b = 0; b < B; ++b)
+      for (size_t t = 0; t < n; ++t) {
+        double d = x[((size_t)b * C + c) * n + t] - m;
+        q += d * d;
+      }
+    mean[c] = m;
+    var[c] = q / N;
+  }
+}
+
+/* One BN on x[B][C][n] in place. The statistics it normalises with go to
+ * mean / var: the batch's (mode 1) or the running ones (mode 0). */
+static void bnb_forward(double* x, int B, int C, size_t n, const double* gam, const double* bet,
+                        const double* rmean, const double* rvar, int mode, double* mean, double* var) {
+  if (mode) {
+    bnb_stats(x, B, C, n, mean, var);
+  } else {
+    memcpy(mean, rmean, sizeof(double) * C);
+    memcpy(var, rvar, sizeof(double) * C);
+  }
+  for (int b = 0; b < B; ++b)
+    for (int c = 0; c < C; ++c) {
+      double sc = gam[c] / sqrt(var[c] + BN_EPS);
+      double* p = x + ((size_t)b * C + c) * n;
+      for (size_t t = 0; t < n; ++t) p[t] = sc * (p[t] - mean[c]) + bet[c];
+    }
+}
+
+/* Adjoint of one BN given its input x and the statistics it used: dgam +=
+ * sum dy xhat, dbet += sum dy, dx += gam / sigma (dy - [sum dy + xhat sum dy
+ * xhat] / N), the bracket only with batch statistics (mode 1), where the
+ * mean and variance are functions of x. */
+static void bnb_backward(const double* x, int B, int C, size_t n, const double* gam, const double* mean,
+                         const double* var, const double* dy, double* dx, double* dgam, double* dbet, int mode) {
+  double N = (double)B * (double)n;
+  for (int c = 0; c < C; ++c) {
+    double is = 1.0 / sqrt(var[c] + BN_EPS), sdy = 0.0, sdx = 0.0;
+    for (int b = 0; b < B; ++b)
+      for (size_t t = 0; t < n; ++t) {
+        size_t i = ((size_t)b * C + c) * n + t;
+        sdy += dy[i];
+        sdx += dy[i] * (x[i] - mean[c]) * is;
+      }
+    dgam[c] += sdx;
+    dbet[c] += sdy;
+    if (!dx) continue;
+    for (int b = 0; b < B; ++b)
+      for (size_t t = 0; t < n; ++t) {
+        size_t i = ((size_t)b * C + c) * n + t;
+        double d = dy[i];
+        if (mode) d -= (sdy + (x[i] - mean[c]) * is * sdx) / N;
+        dx[i] += gam[c] * is * d;
+      }
+  }
+}
+
+/* Saved tensors of one block for all windows, and the statistics each BN
+ * used (m1, v1: BN1 ... m, v: main BN). */
+typedef struct {
+  int h, w, H2, W2;
+  double *x, *t1, *t2, *x1, *u, *y, *g, *s;
+  double *m1, *v1, *m2, *v2, *m3, *v3, *m, *v;
+} bblk_tape;
+
+static void conv_batch(int tr, const double* x, int B, int Ci, int H, int W, const double* w, const double* bias,
+                       int Co, int k, int stride, int pad, int groups, double* y, int Ho, int Wo) {
+  for (int b = 0; b < B; ++b) {
+    const double* xb = x + (size_t)b * Ci * H * W;
+    double* yb = y + (size_t)b * Co * Ho * Wo;
+    if (tr)
+      orc_conv_transpose2d(xb, Ci, H, W, w, bias, Co, k, stride, pad, groups, yb);
+    else
+      orc_conv2d(xb, Ci, H, W, w, bias, Co, k, stride, pad, groups, yb);
+  }
+}
+
+static void conv_batch_bwd(int tr, const double* x, int B, int Ci, int H, int W, const double* w, int Co, int k,
+                           int stride, int pad, int groups, const double* dy, double* dx, double* dw, double* db,
+                           int Ho, int Wo) {
+  for (int b = 0; b < B; ++b) {
+    const double* xb = x + (size_t)b * Ci * H * W;
+    const double* dyb = dy + (size_t)b * Co * Ho * Wo;
+    double* dxb = dx ? dx + (size_t)b * Ci * H * W : NULL;
+    if (tr)
+      conv_transpose2d_bwd(xb, Ci, H, W, w, Co, k, stride, pad, groups, dyb, dxb, dw, db);
+    else
+      conv2d_bwd(xb, Ci, H, W, w, Co, k, stride, pad, groups, dyb, dxb, dw, db);
+  }
+}
+
+/* Block forward over the batch (the arithmetic of block_forward_tape). */
+static double* bblk_forward(const orc_blk* k, const double* x, int B, int h, int w, int mode, bblk_tape* T) {
+  int ci = k->cin, co = k->cout, tr = !k->enc;
+  size_t n = (size_t)h * w, sz = (size_t)B * ci * n;
+  T->h = h;
+  T->w = w;
+  T->H2 = k->enc ? h / 2 : 2 * h;
+  T->W2 = k->enc ? w / 2 : 2 * w;
+  size_t n2 = (size_t)T->H2 * T->W2, sz2 = (size_t)B * co * n2;
+  T->m1 = malloc(sizeof(double) * ci); T->v1 = malloc(sizeof(double) * ci);
+  T->m2 = malloc(sizeof(double) * ci); T->v2 = malloc(sizeof(double) * ci);
+  T->m3 = malloc(sizeof(double) * ci); T->v3 = malloc(sizeof(double) * ci);
+  T->m = malloc(sizeof(double) * co); T->v = malloc(sizeof(double) * co);
+  T->x = dup(x, sz);
+  T->t1 = malloc(sizeof(double) * sz);
+  T->t2 = malloc(sizeof(double) * sz);
+  conv_batch(tr, x, B, ci, h, w, k->w1, NULL, ci, 1, 1, 0, ci, T->t1, h, w);
+  conv_batch(tr, x, B, ci, h, w, k->w3, NULL, ci, 3, 1, 1, ci, T->t2, h, w);
+  double* b1 = dup(T->t1, sz);
+  double* b2 = dup(T->t2, sz);
+  double* b3 = dup(x, sz);
+  bnb_forward(b1, B, ci, n, k->g1, k->b1, k->m1, k->v1, mode, T->m1, T->v1);
+  bnb_forward(b2, B, ci, n, k->g2, k->b2, k->m2, k->v2, mode, T->m2, T->v2);
+  bnb_forward(b3, B, ci, n, k->g3, k->b3, k->m3, k->v3, mode, T->m3, T->v3);
+  T->x1 = malloc(sizeof(double) * sz);
+  for (size_t t = 0; t < sz; ++t) T->x1[t] = b1[t] + b2[t] + b3[t];
+  relu(T->x1, sz);
+  free(b1); free(b2); free(b3);
+  T->u = malloc(sizeof(double) * sz2);
+  double* rs = malloc(sizeof(double) * sz2);
+  conv_batch(tr, T->x1, B, ci, h, w, k->w2, NULL, co, k->enc ? 3 : 4, 2, 1, 1, T->u, T->H2, T->W2);
+  conv_batch(tr, x, B, ci, h, w, k->rw, k->rb, co, k->enc ? 3 : 4, 2, 1, 1, rs, T->H2, T->W2);
+  T->y = dup(T->u, sz2);
+  bnb_forward(T->y, B, co, n2, k->g, k->b, k->m, k->v, mode, T->m, T->v);
+  relu(T->y, sz2);
+  for (size_t t = 0; t < sz2; ++t) T->y[t] += rs[t];
+  free(rs);
+  /* ECA per window */
+  T->g = malloc(sizeof(double) * B * co);
+  T->s = malloc(sizeof(double) * B * co);
+  double* out = malloc(sizeof(double) * sz2);
+  for (int b = 0; b < B; ++b) {
+    const double* yb = T->y + (size_t)b * co * n2;
+    double *g = T->g + (size_t)b * co, *sc = T->s + (size_t)b * co;
+    for (int c = 0; c < co; ++c) {
+      double a = 0.0;
+      for (size_t t = 0; t < n2; ++t) a += yb[c * n2 + t];
+      g[c] = a / (double)n2;
+    }
+    for (int c = 0; c < co; ++c) {
+      double z = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        int cc = c + j - 1;
+        if (cc >= 0 && cc < co) z += k->eca[j] * g[cc];
+      }
+      sc[c] = 1.0 / (1.0 + exp(-z));
+      for (size_t t = 0; t < n2; ++t) out[(size_t)b * co * n2 + c * n2 + t] = sc[c] * yb[c * n2 + t];
+    }
+  }
+  return out;
+}
+
+/* Block adjoint over the batch (the arithmetic of block_backward, with the
+ * batch-statistics BN adjoint when mode is 1). dx accumulates. */
+static void bblk_backward(const orc_blk* k, const bblk_tape* T, int B, const double* dout, double* dx, blk_grad* G,
+                          int mode) {
+  int ci = k->cin, co = k->cout, h = T->h, w = T->w, H2 = T->H2, W2 = T->W2, tr = !k->enc;
+  size_t n = (size_t)h * w, n2 = (size_t)H2 * W2, sz = (size_t)B * ci * n, sz2 = (size_t)B * co * n2;
+  double* dy = malloc(sizeof(double) * sz2);
+  for (int b = 0; b < B; ++b) {
+    const double* ob = dout + (size_t)b * co * n2;
+    const double* yb = T->y + (size_t)b * co * n2;
+    const double *g = T->g + (size_t)b * co, *sc = T->s + (size_t)b * co;
+    double* dyb = dy + (size_t)b * co * n2;
+    double* dz = calloc(co, sizeof(double));
+    for (int c = 0; c < co; ++c) {
+      double ds = 0.0;
+      for (size_t t = 0; t < n2; ++t) {
+        ds += ob[c * n2 + t] * yb[c * n2 + t];
+        dyb[c * n2 + t] = sc[c] * ob[c * n2 + t];
+      }
+      dz[c] = ds * sc[c] * (1.0 - sc[c]);
+    }
+    for (int c = 0; c < co; ++c)
+      for (int j = 0; j < 3; ++j) {
+        int cc = c + j - 1;
+        if (cc < 0 || cc >= co) continue;
+        G->eca[j] += dz[c] * g[cc];
+        double dg = dz[c] * k->eca[j] / (double)n2;
+        for (size_t t = 0; t < n2; ++t) dyb[cc * n2 + t] += dg;
+      }
+    free(dz);
+  }
+  /* y = ReLU(BN(u)) + res(x) */
+  double* dbn = malloc(sizeof(double) * sz2);
+  for (int b = 0; b < B; ++b)
+    for (int c = 0; c < co; ++c) {
+      double is = 1.0 / sqrt(T->v[c] + BN_EPS);
+      for (size_t t = 0; t < n2; ++t) {
+        size_t i = ((size_t)b * co + c) * n2 + t;
+        double bn = k->g[c] * (T->u[i] - T->m[c]) * is + k->b[c];
+        dbn[i] = bn > 0.0 ? dy[i] : 0.0;
+      }
+    }
+  double* du = calloc(sz2, sizeof(double));
+  bnb_backward(T->u, B, co, n2, k->g, T->m, T->v, dbn, du, G->g, G->b, mode);
+  free(dbn);
+  double* dx1 = calloc(sz, sizeof(double));
+  int kk = k->enc ? 3 : 4;
+  conv_batch_bwd(tr, T->x1, B, ci, h, w, k->w2, co, kk, 2, 1, 1, du, dx1, G->w2, NULL, H2, W2);
+  conv_batch_bwd(tr, T->x, B, ci, h, w, k->rw, co, kk, 2, 1, 1, dy, dx, G->rw, G->rb, H2, W2);
+  free(du);
+  free(dy);
+  /* x1 = ReLU(BN1(t1) + BN2(t2) + BN3(x)) */
+  for (size_t t = 0; t < sz; ++t)
+    if (T->x1[t] <= 0.0) dx1[t] = 0.0;
+  double* dt1 = calloc(sz, sizeof(double));
+  double* dt2 = calloc(sz, sizeof(double));
+  bnb_backward(T->t1, B, ci, n, k->g1, T->m1, T->v1, dx1, dt1, G->g1, G->b1, mode);
+  bnb_backward(T->t2, B, ci, n, k->g2, T->m2, T->v2, dx1, dt2, G->g2, G->b2, mode);
+  bnb_backward(T->x, B, ci, n, k->g3, T->m3, T->v3, dx1, dx, G->g3, G->b3, mode);
+  conv_batch_bwd(tr, T->x, B, ci, h, w, k->w1, ci, 1, 1, 0, ci, dt1, dx, G->w1, NULL, h, w);
+  conv_batch_bwd(tr, T->x, B, ci, h, w, k->w3, ci, 3, 1, 1, ci, dt2, dx, G->w3, NULL, h, w);
+  free(dt1); free(dt2); free(dx1);
+}
+
+static void bblk_free(bblk_tape* T) {
+  free(T->x); free(T->t1); free(T->t2); free(T->x1); free(T->u); free(T->y); free(T->g); free(T->s);
+  free(T->m1); free(T->v1); free(T->m2); free(T->v2); free(T->m3); free(T->v3); free(T->m); free(T->v);
+}
+
+/* Gradient pointers mirroring the canonical parameter layout. */
+static double* grad_layout(double* q, blk_grad* G) {
+  q += 232; /* stem W, gamma, beta */
+  for (int b = 0; b < 6; ++b) {
+    int ci = BLK_CIN[b], co = blk_cout(b);
+    G[b].w1 = q; q += ci;
+    G[b].g1 = q; q += ci;
+    G[b].b1 = q; q += ci;
+    G[b].w3 = q; q += 9 * ci;
+    G[b].g2 = q; q += ci;
+    G[b].b2 = q; q += ci;
+    G[b].g3 = q; q += ci;
+    G[b].b3 = q; q += ci;
+    G[b].w2 = q; q += blk_dense(b);
+    G[b].g = q; q += co;
+    G[b].b = q; q += co;
+    G[b].rw = q; q += blk_dense(b);
+    G[b].rb = q; q += co;
+    G[b].eca = q; q += 3;
+  }
+  return q; /* output conv W, b */
+}
+
+/* MSE training loss over B windows against the targets and its gradient
+ * (canonical order) with BN in training mode (mode 1: batch statistics) or
+ * inference mode (mode 0: running statistics). stats (optional) receives,
+ * in the order and layout of the BN buffers, the mean and variance each BN
+ * normalised with (mode 1: the batch's, biased). Returns NAN on a bad
+ * shape. */
+double orc_loss_grad_bn(const float* params, const float* buffers, const float* in, const float* target, int B,
+                        int H, int W, int mode, double* gparams, double* stats) {
+  if (B < 1 || H <= 0 || W <= 0 || H % 8 || W % 8) return NAN;
+  orc_net net;
+  net_load(&net, params, buffers);
+  int np = orc_num_params();
+  memset(gparams, 0, sizeof(double) * np);
+  blk_grad G[6];
+  double* gout_w = grad_layout(gparams, G);
+  double *gout_b = gout_w + 72, *gstem_w = gparams, *gstem_g = gparams + 216, *gstem_b = gparams + 224;
+  size_t n = (size_t)H * W;
+  double* x = malloc(sizeof(double) * B * 3 * n);
+  for (size_t t = 0; t < (size_t)B * 3 * n; ++t) x[t] = (double)in[t];
+  double* su = malloc(sizeof(double) * B * 8 * n);
+  conv_batch(0, x, B, 3, H, W, net.stem_w, NULL, 8, 3, 1, 1, 1, su, H, W);
+  double sm[8], sv[8];
+  double* a0 = dup(su, (size_t)B * 8 * n);
+  bnb_forward(a0, B, 8, n, net.stem_g, net.stem_b, net.stem_m, net.stem_v, mode, sm, sv);
+  relu(a0, (size_t)B * 8 * n);
+  bblk_tape T[6];
+  double* outs[6];
+  const double* a = a0;
+  int h = H, w = W;
+  for (int b = 0; b < 6; ++b) {
+    outs[b] = bblk_forward(&net.blk[b], a, B, h, w, mode, &T[b]);
+    size_t sz = (size_t)B * net.blk[b].cout * T[b].H2 * T[b].W2;
+    if (b == 3 || b == 4) {
+      const double* s = outs[4 - b];
+      for (size_t t = 0; t < sz; ++t) outs[b][t] += s[t];
+    }
+    a = outs[b];
+    h = T[b].H2;
+    w = T[b].W2;
+  }
+  /* output conv, sigmoid, MSE */
+  double* zl = malloc(sizeof(double) * B * n);
+  conv_batch(0, a, B, 8, H, W, net.out_w, net.out_b, 1, 3, 1, 1, 1, zl, H, W);
+  double loss = 0.0, N = (double)B * (double)n;
+  double* dzl = malloc(sizeof(double) * B * n);
+  for (size_t t = 0; t < (size_t)B * n; ++t) {
+    double z = 1.0 / (1.0 + exp(-zl[t])), e = z - (double)target[t];
+    loss += e * e / N;
+    dzl[t] = 2.0 * e / N * z * (1.0 - z);
+  }
+  double* dcur = calloc((size_t)B * 8 * n, sizeof(double));
+  conv_batch_bwd(0, a, B, 8, H, W, net.out_w, 1, 3, 1, 1, 1, dzl, dcur, gout_w, gout_b, H, W);
+  free(zl);
+  free(dzl);
+  double* dskip[2] = {calloc((size_t)B * 16 * (H / 2) * (W / 2), sizeof(double)),
+                      calloc((size_t)B * 32 * (H / 4) * (W / 4), sizeof(double))};
+  for (int b = 5; b >= 0; --b) {
+    size_t osz = (size_t)B * net.blk[b].cout * T[b].H2 * T[b].W2;
+    if (b == 0 || b == 1)
+      for (size_t t = 0; t < osz; ++t) dcur[t] += dskip[b][t];
+    if (b == 3 || b == 4)
+      for (size_t t = 0; t < osz; ++t) dskip[4 - b][t] += dcur[t];
+    double* dx = calloc((size_t)B * net.blk[b].cin * T[b].h * T[b].w, sizeof(double));
+    bblk_backward(&net.blk[b], &T[b], B, dcur, dx, &G[b], mode);
+    free(dcur);
+    dcur = dx;
+  }
+  /* stem: a0 = ReLU(BN(su)) */
+  for (size_t t = 0; t < (size_t)B * 8 * n; ++t)
+    if (a0[t] <= 0.0) dcur[t] = 0.0;
+  double* dsu = calloc((size_t)B * 8 * n, sizeof(double));
+  bnb_backward(su, B, 8, n, net.stem_g, sm, sv, dcur, dsu, gstem_g, gstem_b, mode);
+  conv_batch_bwd(0, x, B, 3, H, W, net.stem_w, 8, 3, 1, 1, 1, dsu, NULL, gstem_w, NULL, H, W);
+  if (stats) {
+    double* q = stats;
+    memcpy(q, sm, sizeof(sm)); q += 8;
+    memcpy(q, sv, sizeof(sv)); q += 8;
+    for (int b = 0; b < 6; ++b) {
+      int ci = BLK_CIN[b], co = blk_cout(b);
+      const double* mv[8] = {T[b].m1, T[b].v1, T[b].m2, T[b].v2, T[b].m3, T[b].v3, T[b].m, T[b].v};
+      for (int j = 0; j < 8; ++j) {
+        int c = j < 6 ? ci : co;
+        memcpy(q, mv[j], sizeof(double) * c);
+        q += c;
+      }
+    }
+  }
+  free(dsu); free(dcur); free(su); free(a0); free(x);
+  for (int b = 0; b < 6; ++b) {
+    bblk_free(&T[b]);
+    free(outs[b]);
+  }
+  free(dskip[0]);
+  free(dskip[1]);
+  net_free(&net);
+  return loss;
+}
+
+/* ======================================================================== */
 /* Metrics (Sec. V-B).                                                      */
 /* ======================================================================== */
 

@@ -109,6 +109,15 @@ int orc_forward_batch(const float* params, const float* buffers,
                       const float* in, int B, int H, int W, double* out,
                       int nthreads);
 
+/* Training step with BN in training mode (mode 1: each BN normalises with
+ * the mean and biased variance of its input over the whole batch) or with
+ * the running statistics (mode 0, equal to orc_loss_grad): MSE over B
+ * windows in[B][3][H][W] against target[B][H][W]; gparams[num_params];
+ * stats (optional, [num_buffers]) receives each BN's mean and variance in
+ * the BN-buffer layout. Returns the loss (NAN on a bad shape). */
+double orc_loss_grad_bn(const float* params, const float* buffers, const float* in, const float* target, int B,
+                        int H, int W, int mode, double* gparams, double* stats);
+
 /* Primitive operations, exposed for pins. */
 void orc_conv2d(const double* x, int Ci, int H, int W, const double* w,
                 const double* bias, int Co, int k, int stride, int pad,

@@ -20,8 +20,12 @@ def torch_reference(params, buffers, x, requires_grad=False):
     return out.detach().numpy(), [b.detach().numpy() for b in blocks]
 
 
-def torch_forward(params, buffers, x, requires_grad=False):
-    frames = int(np.shape(x)[0])  # stacked maps (3 in the paper; 2 or 4 in the fusion variants)
+def torch_forward(params, buffers, x, requires_grad=False, bn_training=False, stats=None):
+    """x [frames][H][W] (one window) or [B][frames][H][W] (a batch). With
+    bn_training every BN normalises with its input's batch statistics
+    (appended to `stats` as (mean, biased var) when given)."""
+    batched = np.ndim(x) == 4
+    frames = int(np.shape(x)[1 if batched else 0])  # stacked maps (3 in the paper; 2 or 4 in the fusion variants)
     P = {k: torch.tensor(params[o:o + s].astype(np.float64), requires_grad=requires_grad)
          for k, (o, s) in I.param_offsets(frames).items()}
     bufs, off = {}, 0
@@ -31,11 +35,16 @@ def torch_forward(params, buffers, x, requires_grad=False):
         off += 2 * c
 
     def bn(t, name):
+        if bn_training:
+            if stats is not None:
+                stats.append((t.mean(dim=(0, 2, 3)), t.var(dim=(0, 2, 3), unbiased=False)))
+            return F.batch_norm(t, None, None, P[name + ".gamma"], P[name + ".beta"], training=True, eps=1e-5)
         m, v = bufs[name]
         return F.batch_norm(t, m, v, P[name + ".gamma"], P[name + ".beta"], training=False, eps=1e-5)
 
     a = x if isinstance(x, torch.Tensor) else torch.tensor(np.asarray(x, np.float64))
-    a = a[None]
+    if not batched:
+        a = a[None]
     a = F.relu(bn(F.conv2d(a, P["stem.w"].view(8, frames, 3, 3), padding=1), "stem.bn"))
     skips, blocks = [], []
     for b in range(6):
@@ -64,4 +73,4 @@ def torch_forward(params, buffers, x, requires_grad=False):
         blocks.append(y[0])
         a = y
     out = torch.sigmoid(F.conv2d(a, P["out.w"].view(1, 8, 3, 3), P["out.b"], padding=1))
-    return out[0, 0], blocks, P
+    return (out[:, 0] if batched else out[0, 0]), blocks, P
