@@ -408,26 +408,35 @@ def main():
         tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, rank * wt.batch, wt.batch, dtype=torch.bfloat16)
         for _ in range(2):
             tctx.backward(tx, target=tclean)
-        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.train_steps)]
-        barrier()
-        for i in range(args.train_steps):
-            flush.fill_(i & 0xFF)
-            tev[i][0].record(stream)
-            tctx.backward(tx, target=tclean)
-            tev[i][1].record(stream)
-        barrier()
-        tms = [a.elapsed_time(b) for a, b in tev]
-        ttot = sum(tms)
-        if dist:
-            t = torch.tensor([ttot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ttot = float(t.item())
+        def time_steps(step):
+            tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.train_steps)]
+            barrier()
+            for i in range(args.train_steps):
+                flush.fill_(i & 0xFF)
+                tev[i][0].record(stream)
+                step()
+                tev[i][1].record(stream)
+            barrier()
+            tms = [a.elapsed_time(b) for a, b in tev]
+            ttot = sum(tms)
+            if dist:
+                t = torch.tensor([ttot], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ttot = float(t.item())
+            return ttot, tms
+
+        ttot, tms = time_steps(lambda: tctx.backward(tx, target=tclean))
+        tctx.backward_bn(tx, target=tclean, mode="batch")
+        btot, _ = time_steps(lambda: tctx.backward_bn(tx, target=tclean, mode="batch"))
         train = {"value": world * wt.batch * args.train_steps / (ttot / 1e3), "unit": UNIT,
                  "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
                  "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
                  "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
-                 "l2": "flushed between timed steps"}
+                 "l2": "flushed between timed steps",
+                 "bn_batch_statistics": {"value": world * wt.batch * args.train_steps / (btot / 1e3),
+                                         "ms_per_step": btot / args.train_steps,
+                                         "step": "the same with BatchNorm in training mode (batch statistics)"}}
         del tctx
 
     hbm_gbs, bf16_tf, bf16_tf_sus, peak_src = load_peaks()

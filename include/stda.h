@@ -171,7 +171,8 @@ stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
 /* Training step (adjoint of the forward pass): runs the network's forward
  * pass with a tape and its exact adjoint, in FP32 on the CUDA cores, with
  * batch normalisation in inference form (frozen running statistics;
- * gamma and beta receive gradients). Weight and BN gradients are reduced
+ * gamma and beta receive gradients; stda_backward_bn below selects training
+ * mode). Weight and BN gradients are reduced
  * per chunk of four windows in FP32 and across chunks in FP64; the loss is
  * an FP64 sum.
  *   d_in      [B][3][H][W] in the context's element type
@@ -189,6 +190,30 @@ stda_status stda_backward(stda_ctx* ctx, const void* d_in, const void* d_target,
                           const float* d_gout, float* d_gparams, double* d_loss,
                           float* d_gin, float* d_out, int B, int H, int W,
                           struct CUstream_st* stream);
+
+/* BN modes of the training step. */
+typedef enum {
+  STDA_BN_RUNNING = 0, /* inference form: the running statistics (frozen) */
+  STDA_BN_BATCH = 1    /* training mode: each BN normalises with the mean and
+                          biased variance of its input over the whole batch
+                          (all B windows and pixels of a channel), and the
+                          adjoint carries the dependence of those statistics
+                          on the input:
+                          dx = gamma/sigma (dy - [sum dy + xhat sum dy xhat]/N) */
+} stda_bn_mode;
+
+/* stda_backward with a BN mode. d_bn_stats (optional, [1360] float, device)
+ * receives the mean and variance each BN normalised with, in the layout of
+ * the BN buffers (per BN: mean[C] then var[C]; stem, then per block BN1,
+ * BN2, BN3, BN), from which a caller updates the running statistics (e.g.
+ * running = (1 - m) running + m batch). The statistics are two-pass
+ * (mean, then mean squared deviation), FP32 per chunk of four windows and
+ * FP64 across chunks. STDA_ERR_INVALID_ARG on an unknown mode. */
+stda_status stda_backward_bn(stda_ctx* ctx, const void* d_in, const void* d_target,
+                             const float* d_gout, float* d_gparams, double* d_loss,
+                             float* d_gin, float* d_out, int B, int H, int W,
+                             stda_bn_mode bn_mode, float* d_bn_stats,
+                             struct CUstream_st* stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -653,8 +653,17 @@ __global__ void k_bf16_to_f32_flat(const __nv_bfloat16* a, float* o, long n) {
 stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, const float* d_gout,
                           float* d_gparams, double* d_loss, float* d_gin, float* d_out, int B, int H, int W,
                           cudaStream_t st) {
+  return stda_backward_bn(c, d_in, d_target, d_gout, d_gparams, d_loss, d_gin, d_out, B, H, W, STDA_BN_RUNNING,
+                          nullptr, st);
+}
+
+stda_status stda_backward_bn(stda_ctx* c, const void* d_in, const void* d_target, const float* d_gout,
+                             float* d_gparams, double* d_loss, float* d_gin, float* d_out, int B, int H, int W,
+                             stda_bn_mode bn_mode, float* d_bn_stats, cudaStream_t st) {
   if (c && c->frames != 3) return fail(c, STDA_ERR_UNSUPPORTED, "backward: the training step takes three maps");
   if (!c) return STDA_ERR_INVALID_ARG;
+  if (bn_mode != STDA_BN_RUNNING && bn_mode != STDA_BN_BATCH)
+    return fail(c, STDA_ERR_INVALID_ARG, "backward: unknown BN mode");
   if (B < 0 || B > c->cfg.max_batch) return fail(c, STDA_ERR_SHAPE, "backward: batch out of range");
   if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "backward: H and W must be positive multiples of 8");
   if ((size_t)B * H * W > (size_t)c->cfg.max_batch * c->cfg.H * c->cfg.W)
@@ -689,6 +698,8 @@ stda_status stda_backward(stda_ctx* c, const void* d_in, const void* d_target, c
   a.loss = d_target ? d_loss : nullptr;
   a.gin = d_gin;
   a.z_out = d_out;
+  a.bn_batch = bn_mode == STDA_BN_BATCH;
+  a.bn_stats = d_bn_stats;
   a.B = B;
   a.H = H;
   a.W = W;

@@ -408,6 +408,45 @@ __global__ void k_bn_dx(const float* a, BnP bn, float* out, long total, int C, i
   float v = a[idx] * bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
   out[idx] = accumulate ? out[idx] + v : v;
 }
+// Batch statistics of a BN input x[B][C][n]: part[chunk][c] = sum over the
+// chunk's windows of x (mean == null) or of (x - mean[c])^2.
+__global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__ mean, float* __restrict__ part,
+                          int B, int C, int n) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x, chunk = blockIdx.y;
+  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
+  const float m = mean ? mean[c] : 0.f;
+  float s = 0.f;
+  for (int b = b0; b < b1; ++b) {
+    const float* p = x + ((size_t)b * C + c) * n;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const float d = p[q] - m;
+      s += mean ? d * d : p[q];
+    }
+  }
+  const float r = block_sum(s, sh);
+  if (threadIdx.x == 0) part[(size_t)chunk * C + c] = r;
+}
+// out[c] = (sum over chunks of part[chunk][c]) / N, summed in FP64
+__global__ void k_bn_fin(const float* __restrict__ part, int nchunks, int C, double N, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0;
+  for (int k = 0; k < nchunks; ++k) s += (double)part[(size_t)k * C + c];
+  out[c] = (float)(s / N);
+}
+// Batch-statistics BN adjoint: out (+)= gam / sigma (dy - (sum dy + xhat sum
+// dy xhat) / N), the two sums of this BN being gacc[dbet + c], gacc[dgam + c].
+__global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const double* __restrict__ gacc, long dgam,
+                              long dbet, double N, float* out, long total, int C, int n, int accumulate) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = (idx / n) % C;
+  const float is = rsqrtf(bn.v[c] + 1e-5f), xh = (x[idx] - bn.m[c]) * is;
+  const float corr = (float)((gacc[dbet + c] + (double)xh * gacc[dgam + c]) / N);
+  const float v = bn.g[c] * is * (dy[idx] - corr);
+  out[idx] = accumulate ? out[idx] + v : v;
+}
 // dv = dx1 [x1 > 0]
 __global__ void k_relu_mask(const float* d, const float* act, float* out, long total) {
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -511,8 +550,21 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   const size_t n0 = (size_t)H * W;
   cudaStream_t st = a.stream;
   const float* P = a.params;
-  const float* Q = a.buffers;
+  const int nchunk = cdiv(B, kChunkWin);
+  // BN statistics: the running ones, or (training mode) the batch's, computed
+  // into `bst` (same layout as the running buffers) right before each BN
+  float* bst = ar.f(kNumBuffers);
+  float* spart = ar.f((size_t)64 * nchunk);
+  const float* Q = a.bn_batch ? bst : a.buffers;
   auto bnp = [&](int g, int b, int m, int v) { return BnP{P + g, P + b, Q + m, Q + v}; };
+  auto batch_stats = [&](const float* x, int Cc, int n, int moff, int voff) {
+    if (!run || !a.bn_batch) return;
+    const double N = (double)B * n;
+    k_bn_part<<<dim3(Cc, nchunk), kT, 0, st>>>(x, nullptr, spart, B, Cc, n);
+    k_bn_fin<<<cdiv(Cc, kT), kT, 0, st>>>(spart, nchunk, Cc, N, bst + moff);
+    k_bn_part<<<dim3(Cc, nchunk), kT, 0, st>>>(x, bst + moff, spart, B, Cc, n);
+    k_bn_fin<<<cdiv(Cc, kT), kT, 0, st>>>(spart, nchunk, Cc, N, bst + voff);
+  };
 
   // ---- forward with tape
   float* xin = ar.f((size_t)B * 3 * n0);
@@ -534,6 +586,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   float* su = ar.f((size_t)B * 8 * n0);
   float* a0 = ar.f((size_t)B * 8 * n0);
   conv(xin, P + C.stem_w, nullptr, su, 3, H, W, 8, 3, 1, 1, 1, false, H, W);
+  batch_stats(su, 8, (int)n0, C.stem_m, C.stem_v);
   if (run) {
     long n = (long)B * 8 * n0;
     k_bn<<<grid1(n), kT, 0, st>>>(su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v, n, 8, (int)n0, 1);
@@ -562,6 +615,9 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     t.out = ar.f((size_t)B * co * n2);
     conv(t.x, P + C.w1[b], nullptr, t.t1, ci, h, w, ci, 1, 1, 0, ci, !enc, h, w);
     conv(t.x, P + C.w3[b], nullptr, t.t2, ci, h, w, ci, 3, 1, 1, ci, !enc, h, w);
+    batch_stats(t.t1, ci, (int)n, C.m1[b], C.v1[b]);
+    batch_stats(t.t2, ci, (int)n, C.m2[b], C.v2[b]);
+    batch_stats(t.x, ci, (int)n, C.m3[b], C.v3[b]);
     if (run)
       k_stage1<<<grid1((long)B * ci * n), kT, 0, st>>>(t.t1, t.t2, t.x, t.x1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]),
                                                      bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
@@ -574,6 +630,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       conv(t.x1, P + C.w2[b], nullptr, t.u, ci, h, w, co, 4, 2, 1, 1, true, t.H2, t.W2);
       conv(t.x, P + C.rw[b], P + C.rb[b], t.r, ci, h, w, co, 4, 2, 1, 1, true, t.H2, t.W2);
     }
+    batch_stats(t.u, co, (int)n2, C.m[b], C.v[b]);
     if (run) {
       long tot = (long)B * co * n2;
       k_stage2<<<grid1(tot), kT, 0, st>>>(t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), tot, co, (int)n2);
@@ -599,7 +656,6 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   }
 
   // ---- backward
-  const int nchunk = cdiv(B, kChunkWin);
   double* gacc = ar.d(kNumParams);
   if (run) cudaMemsetAsync(gacc, 0, sizeof(double) * kNumParams, st);
   // largest partial buffer: pairs * k * k per chunk
@@ -638,6 +694,17 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     k_chan_sums<<<dim3(Cc, nchunk), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n);
     if (dbet >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 0, gacc, dbet);
     if (dgam >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 1, gacc, dgam);
+  };
+  // out (+)= dBN input: gam / sigma dy (running statistics), or the batch
+  // adjoint, whose sums of this BN chan() has just added to gacc
+  auto bn_dx = [&](const float* d, const float* x, BnP bn, int dgam, int dbet, float* out, long tot, int Cc, int n,
+                   int accumulate) {
+    if (!run) return;
+    if (a.bn_batch)
+      k_bn_dx_batch<<<grid1(tot), kT, 0, st>>>(d, x, bn, gacc, dgam, dbet, (double)B * n, out, tot, Cc, n,
+                                               accumulate);
+    else
+      k_bn_dx<<<grid1(tot), kT, 0, st>>>(d, bn, out, tot, Cc, n, accumulate);
   };
   // output conv
   float* dcur = ar.f((size_t)B * 8 * n0);
@@ -683,8 +750,8 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       k_relu_bn_mask<<<grid1(tot2), kT, 0, st>>>(dy, t.u, bn, dtmp, tot2, co, n2);
     }
     chan(dtmp, t.u, Q + C.m[b], Q + C.v[b], co, n2, C.g[b], C.be[b]);
+    bn_dx(dtmp, t.u, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), C.g[b], C.be[b], dtmp, tot2, co, n2, 0);
     if (run) {
-      k_bn_dx<<<grid1(tot2), kT, 0, st>>>(dtmp, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), dtmp, tot2, co, n2, 0);
       cudaMemsetAsync(dx1, 0, sizeof(float) * tot, st);
       cudaMemsetAsync(dx, 0, sizeof(float) * tot, st);
     }
@@ -700,12 +767,12 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     chan(dx1, t.t1, Q + C.m1[b], Q + C.v1[b], ci, n, C.g1[b], C.b1[b]);
     chan(dx1, t.t2, Q + C.m2[b], Q + C.v2[b], ci, n, C.g2[b], C.b2[b]);
     chan(dx1, t.x, Q + C.m3[b], Q + C.v3[b], ci, n, C.g3[b], C.b3[b]);
-    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), dx, tot, ci, n, 1);
+    bn_dx(dx1, t.x, bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), C.g3[b], C.b3[b], dx, tot, ci, n, 1);
     // dt1 = dv gam1 / sigma1 -> dw1, dx
-    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), dt, tot, ci, n, 0);
+    bn_dx(dx1, t.t1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), C.g1[b], C.b1[b], dt, tot, ci, n, 0);
     wgrad(t.x, dt, ci, t.h, t.w, ci, 1, 1, 0, ci, !enc, t.h, t.w, C.w1[b]);
     dgrad(dt, P + C.w1[b], dx, ci, t.h, t.w, ci, 1, 1, 0, ci, !enc, t.h, t.w);
-    if (run) k_bn_dx<<<grid1(tot), kT, 0, st>>>(dx1, bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]), dt, tot, ci, n, 0);
+    bn_dx(dx1, t.t2, bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]), C.g2[b], C.b2[b], dt, tot, ci, n, 0);
     wgrad(t.x, dt, ci, t.h, t.w, ci, 3, 1, 1, ci, !enc, t.h, t.w, C.w3[b]);
     dgrad(dt, P + C.w3[b], dx, ci, t.h, t.w, ci, 3, 1, 1, ci, !enc, t.h, t.w);
     dcur = dx;
@@ -714,8 +781,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   const long tot0 = (long)B * 8 * n0;
   if (run) k_relu_mask<<<grid1(tot0), kT, 0, st>>>(dcur, a0, dtmp, tot0);
   chan(dtmp, su, Q + C.stem_m, Q + C.stem_v, 8, (int)n0, C.stem_g, C.stem_b);
-  if (run)
-    k_bn_dx<<<grid1(tot0), kT, 0, st>>>(dtmp, bnp(C.stem_g, C.stem_b, C.stem_m, C.stem_v), dtmp, tot0, 8, (int)n0, 0);
+  bn_dx(dtmp, su, bnp(C.stem_g, C.stem_b, C.stem_m, C.stem_v), C.stem_g, C.stem_b, dtmp, tot0, 8, (int)n0, 0);
   wgrad(xin, dtmp, 3, H, W, 8, 3, 1, 1, 1, false, H, W, C.stem_w);
   if (a.gin) {
     float* gin = ar.f((size_t)B * 3 * n0);
@@ -726,6 +792,8 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     }
   }
   if (run) {
+    if (a.bn_stats)
+      cudaMemcpyAsync(a.bn_stats, Q, sizeof(float) * kNumBuffers, cudaMemcpyDeviceToDevice, st);
     if (a.gparams_f64) cudaMemcpyAsync(a.gparams_f64, gacc, sizeof(double) * kNumParams, cudaMemcpyDeviceToDevice, st);
     if (a.gparams) k_to_f32<<<cdiv(kNumParams, kT), kT, 0, st>>>(gacc, a.gparams, kNumParams);
   }

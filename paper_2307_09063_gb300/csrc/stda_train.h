@@ -18,6 +18,8 @@ struct TrainArgs {
   double* loss;          // MSE (target mode), or null
   float* gin;            // [B][3][H][W] dL/dx, or null
   float* z_out;          // [B][H][W] forward output of the training graph, or null
+  bool bn_batch;         // BN in training mode: normalise with the batch's statistics
+  float* bn_stats;       // [1360] the statistics each BN used (BN-buffer layout), or null
   int B, H, W;
   cudaStream_t stream;
 };

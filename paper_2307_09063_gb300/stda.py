@@ -72,6 +72,8 @@ def lib():
         L.stda_last_error.argtypes = [_VP]
         L.stda_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, _VP]
+        L.stda_backward_bn.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, _VP, _VP]
         L.stda_metrics.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP,
                                    _VP]
@@ -246,6 +248,22 @@ class Context:
                                  _ptr(out), B, H, W, _stream(stream))
         self._check(st)
         return loss, gp, gin, out
+
+    def backward_bn(self, x, target=None, gout=None, mode="batch", stream=None):
+        """stda_backward_bn: (loss or None, dL/dtheta [137915] float, BN
+        statistics [1360] float) with BN in training mode ("batch": batch
+        statistics) or inference form ("running")."""
+        import torch
+
+        B, _, H, W = x.shape
+        dev = x.device
+        gp = torch.empty(num_params(), dtype=torch.float32, device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev) if target is not None else None
+        stats = torch.empty(num_buffers(), dtype=torch.float32, device=dev)
+        st = lib().stda_backward_bn(self.h, _ptr(x), _ptr(target), _ptr(gout), _ptr(gp), _ptr(loss), None, None,
+                                    B, H, W, {"running": 0, "batch": 1}[mode], _ptr(stats), _stream(stream))
+        self._check(st)
+        return loss, gp, stats
 
     # ----------------------------------------------------------- serving
     def submit(self, radar, frame, out, done=None, stream=None):
