@@ -26,113 +26,151 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 inline dim3 grid1(long n) { return dim3(cdiv(n, kT)); }
 
 // ----------------------------------------------------------- forward ops
+// Each thread computes NT consecutive output channels (forward) or input
+// channels (input gradient) of one pixel, so every activation load feeds NT
+// FMAs; NT divides the channels per group (NT = 1 for depthwise convs).
+// Strided transposed taps: only ky = Y + p (mod s) reach an input row
+// (likewise kx), so the loops step by s from that residue.
+
 // y[b][o][Y][X] = bias[o] + sum_{i in group(o), ky, kx} x[b][i][Y s - p + ky][X s - p + kx] w[o][i'][ky][kx]
+template <int NT>
 __global__ void k_conv(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
                        float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
                        int Ho, int Wo) {
+  const int CoT = Co / NT;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * Co * Ho * Wo) return;
-  int X = idx % Wo, Y = (idx / Wo) % Ho, o = (idx / ((long)Wo * Ho)) % Co, b = idx / ((long)Wo * Ho * Co);
-  int cig = Ci / g, gi = o / (Co / g);
-  float acc = bias ? bias[o] : 0.f;
+  if (idx >= (long)B * CoT * Ho * Wo) return;
+  int X = idx % Wo, Y = (idx / Wo) % Ho, o0 = (int)((idx / ((long)Wo * Ho)) % CoT) * NT,
+      b = idx / ((long)Wo * Ho * CoT);
+  int cig = Ci / g, gi = o0 / (Co / g);
+  float acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = bias ? bias[o0 + j] : 0.f;
   for (int il = 0; il < cig; ++il) {
     const float* xp = x + ((size_t)b * Ci + gi * cig + il) * H * W;
-    const float* wp = w + ((size_t)o * cig + il) * k * k;
+    const float* wp = w + ((size_t)o0 * cig + il) * k * k;
     for (int ky = 0; ky < k; ++ky) {
       int yy = Y * s - p + ky;
       if (yy < 0 || yy >= H) continue;
       for (int kx = 0; kx < k; ++kx) {
         int xx = X * s - p + kx;
         if (xx < 0 || xx >= W) continue;
-        acc += xp[yy * W + xx] * wp[ky * k + kx];
+        const float v = xp[yy * W + xx];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] += v * wp[(size_t)j * cig * k * k + ky * k + kx];
       }
     }
   }
-  y[idx] = acc;
+  const size_t plane = (size_t)Ho * Wo;
+  float* yp = y + ((size_t)b * Co + o0) * plane + (size_t)Y * Wo + X;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) yp[j * plane] = acc[j];
 }
 
 // transposed: y[b][o][Y][X] = bias[o] + sum x[b][i][yi][xi] w[i][o'][ky][kx], Y = yi s - p + ky
+template <int NT>
 __global__ void k_convT(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
                         float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
                         int Ho, int Wo) {
+  const int CoT = Co / NT;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * Co * Ho * Wo) return;
-  int X = idx % Wo, Y = (idx / Wo) % Ho, o = (idx / ((long)Wo * Ho)) % Co, b = idx / ((long)Wo * Ho * Co);
-  int cig = Ci / g, cog = Co / g, gi = o / cog, ol = o % cog;
-  float acc = bias ? bias[o] : 0.f;
+  if (idx >= (long)B * CoT * Ho * Wo) return;
+  int X = idx % Wo, Y = (idx / Wo) % Ho, o0 = (int)((idx / ((long)Wo * Ho)) % CoT) * NT,
+      b = idx / ((long)Wo * Ho * CoT);
+  int cig = Ci / g, cog = Co / g, gi = o0 / cog, ol0 = o0 % cog;
+  float acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = bias ? bias[o0 + j] : 0.f;
   for (int il = 0; il < cig; ++il) {
     int i = gi * cig + il;
     const float* xp = x + ((size_t)b * Ci + i) * H * W;
-    const float* wp = w + ((size_t)i * cog + ol) * k * k;
-    for (int ky = 0; ky < k; ++ky) {
-      int ny = Y + p - ky;
-      if (ny < 0 || ny % s) continue;
-      int yi = ny / s;
-      if (yi >= H) continue;
-      for (int kx = 0; kx < k; ++kx) {
-        int nx = X + p - kx;
-        if (nx < 0 || nx % s) continue;
-        int xi = nx / s;
-        if (xi >= W) continue;
-        acc += xp[yi * W + xi] * wp[ky * k + kx];
+    const float* wp = w + ((size_t)i * cog + ol0) * k * k;
+    for (int ky = (Y + p) % s; ky < k; ky += s) {
+      int yi = (Y + p - ky) / s;
+      if (yi < 0 || yi >= H) continue;
+      for (int kx = (X + p) % s; kx < k; kx += s) {
+        int xi = (X + p - kx) / s;
+        if (xi < 0 || xi >= W) continue;
+        const float v = xp[yi * W + xi];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] += v * wp[(size_t)j * k * k + ky * k + kx];
       }
     }
   }
-  y[idx] = acc;
+  const size_t plane = (size_t)Ho * Wo;
+  float* yp = y + ((size_t)b * Co + o0) * plane + (size_t)Y * Wo + X;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) yp[j * plane] = acc[j];
 }
 
 // dx[b][i][yy][xx] += sum over (o, ky, kx) with yy = Y s - p + ky of dy w (adjoint of k_conv)
+template <int NT>
 __global__ void k_conv_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
                              int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
+  const int CiT = Ci / NT;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * Ci * H * W) return;
-  int xx = idx % W, yy = (idx / W) % H, i = (idx / ((long)W * H)) % Ci, b = idx / ((long)W * H * Ci);
-  int cig = Ci / g, cog = Co / g, gi = i / cig, il = i % cig;
-  float acc = 0.f;
+  if (idx >= (long)B * CiT * H * W) return;
+  int xx = idx % W, yy = (idx / W) % H, i0 = (int)((idx / ((long)W * H)) % CiT) * NT,
+      b = idx / ((long)W * H * CiT);
+  int cig = Ci / g, cog = Co / g, gi = i0 / cig, il0 = i0 % cig;
+  float acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = 0.f;
   for (int ol = 0; ol < cog; ++ol) {
     int o = gi * cog + ol;
     const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
-    const float* wp = w + ((size_t)o * cig + il) * k * k;
-    for (int ky = 0; ky < k; ++ky) {
-      int ny = yy + p - ky;
-      if (ny < 0 || ny % s) continue;
-      int Y = ny / s;
-      if (Y >= Ho) continue;
-      for (int kx = 0; kx < k; ++kx) {
-        int nx = xx + p - kx;
-        if (nx < 0 || nx % s) continue;
-        int X = nx / s;
-        if (X >= Wo) continue;
-        acc += dp[Y * Wo + X] * wp[ky * k + kx];
+    const float* wp = w + ((size_t)o * cig + il0) * k * k;
+    for (int ky = (yy + p) % s; ky < k; ky += s) {
+      int Y = (yy + p - ky) / s;
+      if (Y < 0 || Y >= Ho) continue;
+      for (int kx = (xx + p) % s; kx < k; kx += s) {
+        int X = (xx + p - kx) / s;
+        if (X < 0 || X >= Wo) continue;
+        const float d = dp[Y * Wo + X];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] += d * wp[(size_t)j * k * k + ky * k + kx];
       }
     }
   }
-  dx[idx] += acc;
+  const size_t plane = (size_t)H * W;
+  float* xp = dx + ((size_t)b * Ci + i0) * plane + (size_t)yy * W + xx;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) xp[j * plane] += acc[j];
 }
 
 // dx[b][i][yi][xi] += sum_{o', ky, kx} dy[b][o][yi s - p + ky][xi s - p + kx] w[i][o'][ky][kx]
+template <int NT>
 __global__ void k_convT_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
                               int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
+  const int CiT = Ci / NT;
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * Ci * H * W) return;
-  int xi = idx % W, yi = (idx / W) % H, i = (idx / ((long)W * H)) % Ci, b = idx / ((long)W * H * Ci);
-  int cig = Ci / g, cog = Co / g, gi = i / cig;
-  float acc = 0.f;
+  if (idx >= (long)B * CiT * H * W) return;
+  int xi = idx % W, yi = (idx / W) % H, i0 = (int)((idx / ((long)W * H)) % CiT) * NT,
+      b = idx / ((long)W * H * CiT);
+  int cig = Ci / g, cog = Co / g, gi = i0 / cig;
+  float acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = 0.f;
   for (int ol = 0; ol < cog; ++ol) {
     int o = gi * cog + ol;
     const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
-    const float* wp = w + ((size_t)i * cog + ol) * k * k;
+    const float* wp = w + ((size_t)i0 * cog + ol) * k * k;
     for (int ky = 0; ky < k; ++ky) {
       int Y = yi * s - p + ky;
       if (Y < 0 || Y >= Ho) continue;
       for (int kx = 0; kx < k; ++kx) {
         int X = xi * s - p + kx;
         if (X < 0 || X >= Wo) continue;
-        acc += dp[Y * Wo + X] * wp[ky * k + kx];
+        const float d = dp[Y * Wo + X];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] += d * wp[(size_t)j * cog * k * k + ky * k + kx];
       }
     }
   }
-  dx[idx] += acc;
+  const size_t plane = (size_t)H * W;
+  float* xp = dx + ((size_t)b * Ci + i0) * plane + (size_t)yi * W + xi;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) xp[j * plane] += acc[j];
 }
 
 __device__ float block_sum(float v, float* sh) {
@@ -151,10 +189,13 @@ __device__ float block_sum(float v, float* sh) {
 // Weight gradient of one (output, input) channel pair of a conv (or of a
 // transposed conv when T) over the windows of one chunk: one block per pair,
 // k*k sums per thread, block reduction; part[chunk][pair * k * k + tap].
-template <bool TR>
+// K is the kernel size (1, 3 or 4) as a template argument, so the k * k sums
+// stay in registers.
+template <bool TR, int K>
 __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ part,
-                        int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo,
+                        int B, int Ci, int H, int W, int Co, int s, int p, int g, int Ho, int Wo,
                         int npairs) {
+  constexpr int k = K;
   __shared__ float sh[32];
   const int pair = blockIdx.x, chunk = blockIdx.y;
   const int cig = Ci / g, cog = Co / g;
@@ -166,9 +207,9 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
     i = pair / cog;
     o = (i / cig) * cog + pair % cog;
   }
-  float acc[16];
+  float acc[K * K];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.f;
+  for (int t = 0; t < K * K; ++t) acc[t] = 0.f;
   const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
   if (!TR) {
     const int n = Ho * Wo;
@@ -178,9 +219,11 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
       for (int q = threadIdx.x; q < n; q += blockDim.x) {
         int Y = q / Wo, X = q % Wo;
         float d = dp[q];
+#pragma unroll
         for (int ky = 0; ky < k; ++ky) {
           int yy = Y * s - p + ky;
           if (yy < 0 || yy >= H) continue;
+#pragma unroll
           for (int kx = 0; kx < k; ++kx) {
             int xx = X * s - p + kx;
             if (xx < 0 || xx >= W) continue;
@@ -197,9 +240,11 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
       for (int q = threadIdx.x; q < n; q += blockDim.x) {
         int yi = q / W, xi = q % W;
         float v = xp[q];
+#pragma unroll
         for (int ky = 0; ky < k; ++ky) {
           int Y = yi * s - p + ky;
           if (Y < 0 || Y >= Ho) continue;
+#pragma unroll
           for (int kx = 0; kx < k; ++kx) {
             int X = xi * s - p + kx;
             if (X < 0 || X >= Wo) continue;
@@ -209,6 +254,7 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
       }
     }
   }
+#pragma unroll
   for (int t = 0; t < k * k; ++t) {
     float r = block_sum(acc[t], sh);
     if (threadIdx.x == 0) part[(size_t)chunk * npairs * k * k + (size_t)pair * k * k + t] = r;
@@ -577,11 +623,16 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    long n = (long)B * Co * Ho * Wo;
-    if (tr)
-      k_convT<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+    const bool t4 = (Co / g) % 4 == 0;
+    long n = (long)B * (t4 ? Co / 4 : Co) * Ho * Wo;
+    if (tr && t4)
+      k_convT<4><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+    else if (tr)
+      k_convT<1><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+    else if (t4)
+      k_conv<4><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
     else
-      k_conv<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+      k_conv<1><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
   };
   float* su = ar.f((size_t)B * 8 * n0);
   float* a0 = ar.f((size_t)B * 8 * n0);
@@ -671,21 +722,26 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     if (!run) return;
     int npairs = tr ? Ci * (Co / g) : Co * (Ci / g);
     dim3 grid(npairs, nchunk);
-    if (tr)
-      k_wgrad<true><<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo, npairs);
-    else
-      k_wgrad<false><<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo, npairs);
+    auto go = [&](auto kern) { kern<<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, s, p, g, Ho, Wo, npairs); };
+    if (k == 1) tr ? go(k_wgrad<true, 1>) : go(k_wgrad<false, 1>);
+    else if (k == 3) tr ? go(k_wgrad<true, 3>) : go(k_wgrad<false, 3>);
+    else tr ? go(k_wgrad<true, 4>) : go(k_wgrad<false, 4>);
     int n = npairs * k * k;
     k_reduce<<<cdiv(n, kT), kT, 0, st>>>(part, nchunk, n, 1, 0, gacc, dst);
   };
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    long n = (long)B * Ci * hh * ww;
-    if (tr)
-      k_convT_dgrad<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+    const bool t4 = (Ci / g) % 4 == 0;
+    long n = (long)B * (t4 ? Ci / 4 : Ci) * hh * ww;
+    if (tr && t4)
+      k_convT_dgrad<4><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+    else if (tr)
+      k_convT_dgrad<1><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+    else if (t4)
+      k_conv_dgrad<4><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
     else
-      k_conv_dgrad<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+      k_conv_dgrad<1><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
   };
   // per-channel sums of (a) and (a * normalised v) -> dbeta / dgamma (and bias)
   auto chan = [&](const float* av, const float* v, const float* mean, const float* var, int Cc, int n,
