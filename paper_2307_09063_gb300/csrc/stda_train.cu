@@ -623,16 +623,13 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    const bool t4 = (Co / g) % 4 == 0;
-    long n = (long)B * (t4 ? Co / 4 : Co) * Ho * Wo;
-    if (tr && t4)
-      k_convT<4><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
-    else if (tr)
-      k_convT<1><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
-    else if (t4)
-      k_conv<4><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+    const int nt = (Co / g) % 8 == 0 ? 8 : (Co / g) % 4 == 0 ? 4 : 1;
+    long n = (long)B * (Co / nt) * Ho * Wo;
+    auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo); };
+    if (tr)
+      nt == 8 ? go(k_convT<8>) : nt == 4 ? go(k_convT<4>) : go(k_convT<1>);
     else
-      k_conv<1><<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo);
+      nt == 8 ? go(k_conv<8>) : nt == 4 ? go(k_conv<4>) : go(k_conv<1>);
   };
   float* su = ar.f((size_t)B * 8 * n0);
   float* a0 = ar.f((size_t)B * 8 * n0);
@@ -732,16 +729,13 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    const bool t4 = (Ci / g) % 4 == 0;
-    long n = (long)B * (t4 ? Ci / 4 : Ci) * hh * ww;
-    if (tr && t4)
-      k_convT_dgrad<4><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
-    else if (tr)
-      k_convT_dgrad<1><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
-    else if (t4)
-      k_conv_dgrad<4><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+    const int nt = (Ci / g) % 8 == 0 ? 8 : (Ci / g) % 4 == 0 ? 4 : 1;
+    long n = (long)B * (Ci / nt) * hh * ww;
+    auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo); };
+    if (tr)
+      nt == 8 ? go(k_convT_dgrad<8>) : nt == 4 ? go(k_convT_dgrad<4>) : go(k_convT_dgrad<1>);
     else
-      k_conv_dgrad<1><<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo);
+      nt == 8 ? go(k_conv_dgrad<8>) : nt == 4 ? go(k_conv_dgrad<4>) : go(k_conv_dgrad<1>);
   };
   // per-channel sums of (a) and (a * normalised v) -> dbeta / dgamma (and bias)
   auto chan = [&](const float* av, const float* v, const float* mean, const float* var, int Cc, int n,
