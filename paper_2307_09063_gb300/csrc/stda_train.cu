@@ -186,30 +186,38 @@ __device__ float block_sum(float v, float* sh) {
   return r;  // valid in thread 0
 }
 
-// Weight gradient of one (output, input) channel pair of a conv (or of a
-// transposed conv when T) over the windows of one chunk: one block per pair,
-// k*k sums per thread, block reduction; part[chunk][pair * k * k + tap].
-// K is the kernel size (1, 3 or 4) as a template argument, so the k * k sums
-// stay in registers.
-template <bool TR, int K>
+// Weight gradient of NT channel pairs of a conv (or of a transposed conv
+// when TR) over the windows of one chunk: one block per pair tile, the
+// shared operand (dy of output o for a conv, x of input i for a transposed
+// conv) loaded once per pixel for the NT pairs; per value a warp shuffle
+// reduction, then one pass over the warps; part[chunk][pair * k * k + tap].
+// K is the kernel size (1, 3 or 4) as a template argument, so the sums stay
+// in registers.
+template <bool TR, int K, int NT>
 __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ part,
                         int B, int Ci, int H, int W, int Co, int s, int p, int g, int Ho, int Wo,
                         int npairs) {
-  constexpr int k = K;
-  __shared__ float sh[32];
-  const int pair = blockIdx.x, chunk = blockIdx.y;
+  constexpr int k = K, KK = K * K, NV = NT * KK;
+  __shared__ float sh[32 * NV];
+  const int tile = blockIdx.x, chunk = blockIdx.y;
   const int cig = Ci / g, cog = Co / g;
-  int i, o;
-  if (!TR) {  // pair = o * cig + il
-    o = pair / cig;
-    i = (o / cog) * cig + pair % cig;
-  } else {    // pair = i * cog + ol
-    i = pair / cog;
-    o = (i / cig) * cog + pair % cog;
+  int i, o, pair0;
+  if (!TR) {  // pairs o * cig + il, il = il0 .. il0 + NT - 1
+    o = tile / (cig / NT);
+    const int il0 = (tile % (cig / NT)) * NT;
+    i = (o / cog) * cig + il0;
+    pair0 = o * cig + il0;
+  } else {    // pairs i * cog + ol, ol = ol0 .. ol0 + NT - 1
+    i = tile / (cog / NT);
+    const int ol0 = (tile % (cog / NT)) * NT;
+    o = (i / cig) * cog + ol0;
+    pair0 = i * cog + ol0;
   }
-  float acc[K * K];
+  float acc[NT][KK];
 #pragma unroll
-  for (int t = 0; t < K * K; ++t) acc[t] = 0.f;
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int t = 0; t < KK; ++t) acc[j][t] = 0.f;
   const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
   if (!TR) {
     const int n = Ho * Wo;
@@ -227,7 +235,8 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
           for (int kx = 0; kx < k; ++kx) {
             int xx = X * s - p + kx;
             if (xx < 0 || xx >= W) continue;
-            acc[ky * k + kx] += d * xp[yy * W + xx];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) acc[j][ky * k + kx] += d * xp[(size_t)j * H * W + yy * W + xx];
           }
         }
       }
@@ -248,16 +257,28 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
           for (int kx = 0; kx < k; ++kx) {
             int X = xi * s - p + kx;
             if (X < 0 || X >= Wo) continue;
-            acc[ky * k + kx] += v * dp[Y * Wo + X];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) acc[j][ky * k + kx] += v * dp[(size_t)j * Ho * Wo + Y * Wo + X];
           }
         }
       }
     }
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int t = 0; t < k * k; ++t) {
-    float r = block_sum(acc[t], sh);
-    if (threadIdx.x == 0) part[(size_t)chunk * npairs * k * k + (size_t)pair * k * k + t] = r;
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+      float v = acc[j][t];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) sh[warp * NV + j * KK + t] = v;
+    }
+  __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    float r = 0.f;
+    for (int w = 0; w < nw; ++w) r += sh[w * NV + v];
+    part[(size_t)chunk * npairs * KK + (size_t)pair0 * KK + v] = r;
   }
 }
 
@@ -718,11 +739,23 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
                    bool tr, int Ho, int Wo, int dst) {
     if (!run) return;
     int npairs = tr ? Ci * (Co / g) : Co * (Ci / g);
-    dim3 grid(npairs, nchunk);
+    // pairs per block: 4 where the tiled dimension (Ci / g for a conv,
+    // Co / g for a transposed conv) allows
+    // (2 for the 4x4 kernels, whose 16 sums per pair cost registers)
+    const int tdim = tr ? Co / g : Ci / g;
+    const int nt = tdim % 4 == 0 ? (k == 4 ? 2 : 4) : 1;
+    dim3 grid(npairs / nt, nchunk);
     auto go = [&](auto kern) { kern<<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, s, p, g, Ho, Wo, npairs); };
-    if (k == 1) tr ? go(k_wgrad<true, 1>) : go(k_wgrad<false, 1>);
-    else if (k == 3) tr ? go(k_wgrad<true, 3>) : go(k_wgrad<false, 3>);
-    else tr ? go(k_wgrad<true, 4>) : go(k_wgrad<false, 4>);
+    if (nt == 4) {
+      if (k == 1) tr ? go(k_wgrad<true, 1, 4>) : go(k_wgrad<false, 1, 4>);
+      else tr ? go(k_wgrad<true, 3, 4>) : go(k_wgrad<false, 3, 4>);
+    } else if (nt == 2) {
+      tr ? go(k_wgrad<true, 4, 2>) : go(k_wgrad<false, 4, 2>);
+    } else {
+      if (k == 1) tr ? go(k_wgrad<true, 1, 1>) : go(k_wgrad<false, 1, 1>);
+      else if (k == 3) tr ? go(k_wgrad<true, 3, 1>) : go(k_wgrad<false, 3, 1>);
+      else tr ? go(k_wgrad<true, 4, 1>) : go(k_wgrad<false, 4, 1>);
+    }
     int n = npairs * k * k;
     k_reduce<<<cdiv(n, kT), kT, 0, st>>>(part, nchunk, n, 1, 0, gacc, dst);
   };
