@@ -164,7 +164,8 @@ stda_status stda_set_buffers(stda_ctx* ctx, const float* host_src, size_t n);
 /* Denoises B windows: d_in [B][frames][H][W] -> d_out [B][1][H][W] (Sec. IV-A,
  * Eqs. "encoder_stda", "decoder_stda"). H, W may be smaller than the
  * context's, but B*H*W may not exceed max_batch*H_ctx*W_ctx. B == 0 is a
- * no-op. */
+ * no-op. d_in and d_out must be 16-byte aligned (STDA_ERR_INVALID_ARG
+ * otherwise). */
 stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
                          int H, int W, struct CUstream_st* stream);
 

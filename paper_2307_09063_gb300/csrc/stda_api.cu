@@ -610,6 +610,8 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
   if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "forward: H and W must be positive multiples of 8");
   if (B == 0) return STDA_OK;
   if (!d_in || !d_out) return fail(c, STDA_ERR_INVALID_ARG, "forward: null pointer");
+  if (((uintptr_t)d_in | (uintptr_t)d_out) & 15)
+    return fail(c, STDA_ERR_INVALID_ARG, "forward: buffers must be 16-byte aligned");
   size_t es = elem_size(c->cfg.prec);
   if (stda::scratch_bytes(B, H, W, es) > c->scratch_size)
     return fail(c, STDA_ERR_SHAPE, "forward: B*H*W exceeds the context's scratch");

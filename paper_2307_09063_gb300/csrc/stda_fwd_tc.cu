@@ -384,6 +384,16 @@ struct Misc {
   }
 };
 
+// 16-byte asynchronous global -> shared copy (zero-fill when !valid; the
+// source is then not read), and waits for this thread's copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage-1 weights of tap t, channels 4q .. 4q + 3 of group g (layout
 // [tap][quad][group][4]).
 template <int CG>
@@ -537,6 +547,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
   const int items = a.tiles_per_window * a.nwin;
   bool failed = false;
+  // stem: the NF raw maps of an item's rows (with halo) are copied
+  // asynchronously into the input staging area, zero outside the map; the
+  // next item's copy is issued as soon as the stem has consumed this one
+  auto stem_fetch = [&](int it) {
+    if (!STEM || it >= items) return;
+    const int bb = it / a.tiles_per_window, oy = (it % a.tiles_per_window) * TY;
+    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy - 3, nch = CW / 8;
+    __nv_bfloat16* sin = (__nv_bfloat16*)(sm + L.off_in);
+    const __nv_bfloat16* in = a.in + (size_t)bb * NF * h * w;
+    for (int i = tid; i < NF * RI * nch; i += blockDim.x) {
+      const int c = i / (RI * nch), r = (i / nch) % RI, x = (i % nch) * 8 - 8, y = yi0 + r;
+      const bool ok = y >= 0 && y < h && x >= 0 && x < w;
+      cp_async16(sin + (size_t)i * 8, ok ? (const void*)(in + ((size_t)c * h + y) * w + x) : (const void*)in, ok);
+    }
+    cp_async_commit();
+  };
+  stem_fetch(blockIdx.x);
 
   // persistent loop over (window, band) items
   for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
@@ -552,17 +579,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   // x[2r + py][2s + px] at local row r - (oy0 - 1), column s + 1.
   const int y_lo = max(0, 2 * oy0 - 2), y_hi = min(h - 1, 2 * oy0 + 2 * TY + 1);
   if (STEM) {
-    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy0 - 3, nch = CW / 8;
-    __nv_bfloat16* sin = (__nv_bfloat16*)(sm + L.off_in);
-    const __nv_bfloat16* in = a.in + (size_t)b * NF * h * w;
-    batched<8>(
-        NF * RI * nch,
-        [&](int i) {
-          int c = i / (RI * nch), r = (i / nch) % RI, x = (i % nch) * 8 - 8, y = yi0 + r;
-          return (y >= 0 && y < h && x >= 0 && x < w) ? *(const uint4*)(in + ((size_t)c * h + y) * w + x)
-                                                      : make_uint4(0, 0, 0, 0);
-        },
-        [&](int i, uint4 v) { *(uint4*)(sin + (size_t)i * 8) = v; });
+    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy0 - 3;
+    const __nv_bfloat16* sin = (const __nv_bfloat16*)(sm + L.off_in);
+    cp_async_wait_all();  // this item's rows (issued during the previous item)
     __syncthreads();
     // stem conv NF -> 8: four horizontally adjacent positions per thread share
     // the weight loads; channel pairs go through packed FP32 FMAs
@@ -649,6 +668,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
     }
   }
   __syncthreads();
+  stem_fetch(item + gridDim.x);  // the staging area is free again
   // 2. stage 1 at the rows the stride-2 taps read: y in [2 oy0 - 1, 2 oy0 + 2 TY - 1].
   // Item = (pixel pair (y, x), (y, x + 1) with x even, group g): the pair
   // reads columns x - 1 .. x + 2 of three rows, 12 plane pixels for 18 taps.
@@ -747,6 +767,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   }
   __syncthreads();
   }  // item loop
+  if (STEM) cp_async_wait_all();  // copies issued for an item past a failure
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
