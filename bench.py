@@ -50,6 +50,37 @@ FFMA_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ / 1e3  # 80.5
 FP8_OVER_BF16 = 4.5 / 2.25  # nominal dense ratio
 
 
+def dist_env():
+    """(world, rank, local rank) of this process (torchrun sets the
+    variables; a plain run is world 1, rank 0)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def first_window(rank: int, per_rank: int) -> int:
+    """Windows are sharded by rank with no exchange: rank r generates and
+    denoises windows r * per_rank .. (r + 1) * per_rank - 1."""
+    return rank * per_rank
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); the value itself without torch.distributed."""
+    if not dist:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, per_rank: int, steps: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the
+    slowest rank's time."""
+    return world * per_rank * steps / (max_ms / 1e3)
+
+
 def ncu_traffic(workload: str, kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of this
     workload (profiles/ncu_tc_<workload>.md), or None when there is none or
@@ -307,9 +338,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if args.workload == "serving":
         return main_serving(args, world, rank, local)
     w = workload(args.workload)
@@ -338,7 +367,7 @@ def main():
     dtype = torch.float32 if w.precision == "fp32" else torch.bfloat16
     esz = 4 if w.precision == "fp32" else 2
     ctx = stda.Context(H, W, B, w.precision, 0)
-    x, _, _, _ = stda.generate(g, 0, w.cid, rank * B, B, dtype=dtype, with_clean=False)
+    x, _, _, _ = stda.generate(g, 0, w.cid, first_window(rank, B), B, dtype=dtype, with_clean=False)
     out = torch.empty((B, 1, H, W), dtype=dtype, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -368,13 +397,9 @@ def main():
     kt = ctx.profile_read()
     ctx.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = reduce_max(sum(step_ms), dist, dev)
     ms_per_step = tot_ms / args.steps
-    value = world * B * args.steps / (tot_ms / 1e3)
+    value = whole_job_rate(world, B, args.steps, tot_ms)
 
     # end to end through the public API: pinned host input -> device, forward,
     # device -> pinned host output, every step
@@ -392,11 +417,8 @@ def main():
         ev2[i][1].record(stream)
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * B * args.steps / (e2e_ms / 1e3)
+    e2e_ms = reduce_max(e2e_ms, dist, dev)
+    e2e_value = whole_job_rate(world, B, args.steps, e2e_ms)
 
     # fwd + bwd: the training step (stda_backward, MSE against the clean maps)
     # on 64 windows of 3 x 256 x 128, one step per timed iteration
@@ -405,7 +427,7 @@ def main():
         wt = workload("train_bf16_b64_3x256x128")
         gt = wt.gen
         tctx = stda.Context(gt.P, gt.Q, wt.batch, "bf16", 0)
-        tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, rank * wt.batch, wt.batch, dtype=torch.bfloat16)
+        tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, first_window(rank, wt.batch), wt.batch, dtype=torch.bfloat16)
         for _ in range(2):
             tctx.backward(tx, target=tclean)
         def time_steps(step):
@@ -419,22 +441,17 @@ def main():
                 tev[i][1].record(stream)
             barrier()
             tms = [a.elapsed_time(b) for a, b in tev]
-            ttot = sum(tms)
-            if dist:
-                t = torch.tensor([ttot], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ttot = float(t.item())
-            return ttot, tms
+            return reduce_max(sum(tms), dist, dev), tms
 
         ttot, tms = time_steps(lambda: tctx.backward(tx, target=tclean))
         tctx.backward_bn(tx, target=tclean, mode="batch")
         btot, _ = time_steps(lambda: tctx.backward_bn(tx, target=tclean, mode="batch"))
-        train = {"value": world * wt.batch * args.train_steps / (ttot / 1e3), "unit": UNIT,
+        train = {"value": whole_job_rate(world, wt.batch, args.train_steps, ttot), "unit": UNIT,
                  "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
                  "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
                  "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
                  "l2": "flushed between timed steps",
-                 "bn_batch_statistics": {"value": world * wt.batch * args.train_steps / (btot / 1e3),
+                 "bn_batch_statistics": {"value": whole_job_rate(world, wt.batch, args.train_steps, btot),
                                          "ms_per_step": btot / args.train_steps,
                                          "step": "the same with BatchNorm in training mode (batch statistics)"}}
         del tctx

@@ -183,4 +183,6 @@ def test_invalid_calls_return_status(stda):
     assert ctx.forward_raw(x, y, 1, 12, 32) == stda.ERR_SHAPE   # not a multiple of 8
     assert ctx.forward_raw(x, y, 1, 64, 64) == stda.ERR_SHAPE   # larger than the context
     assert ctx.forward_raw(None, y, 1, 32, 32) == stda.ERR_INVALID_ARG
+    flat = torch.zeros(2 * 3 * 32 * 32 + 1, device="cuda")
+    assert ctx.forward_raw(flat[1:].view(2, 3, 32, 32), y, 1, 32, 32) == stda.ERR_INVALID_ARG  # unaligned
     assert ctx.device_status() == stda.OK
