@@ -483,6 +483,17 @@ def main():
                         "flops_per_launch": 2.0 * fma_macs * px},
                 "tensor": {"achieved": tc_tf, "peak": tc_peak, "frac": fr_tc, "flops_per_launch": 2.0 * tc_macs * px},
                 "avg_launch_ms": k_avg_s * 1e3, "time_shares": shares}
+    # the whole step against the binding compute roofline: the dense convs
+    # at the tensor peak and the thin / depthwise / stem / output work at the
+    # FP32 FMA peak, which can run concurrently, so the bound is the larger
+    px_step = B * H * W
+    tc_total = sum(KERNEL_TC_MACS_PER_PX.values()) if w.precision != "fp32" else 0
+    t_tensor_us = 2.0 * tc_total * px_step / (tc_peak * 1e12) * 1e6
+    t_fma_us = 2.0 * (MACS_PER_PX - tc_total) * px_step / (FFMA_PEAK_TFLOPS * 1e12) * 1e6
+    step_roofline = {"t_tensor_us": t_tensor_us, "t_fma_us": t_fma_us, "bound_us": max(t_tensor_us, t_fma_us),
+                     "measured_us": ms_per_step * 1e3,
+                     "frac": max(t_tensor_us, t_fma_us) / (ms_per_step * 1e3),
+                     "peaks": f"tensor {tc_peak:.0f} TFLOP/s, FP32 FMA {FFMA_PEAK_TFLOPS:.1f} TFLOP/s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3x2"}.get(w.precision, w.precision),
@@ -495,6 +506,7 @@ def main():
                     "bytes_per_step": bytes_per_step, "peak_source": peak_src},
             "compute": {"macs_per_px": MACS_PER_PX, "tflops": 2.0 * MACS_PER_PX * B * H * W / (ms_per_step / 1e3) / 1e12},
             "roofline": roofline,
+            "step_roofline": step_roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * esz),
                     "d2h_bytes_per_step": int(oh.numel() * esz)},
             "clocks": clk.summary(), "gpu_launches": int(launches)}
