@@ -173,6 +173,141 @@ __global__ void k_convT_dgrad(const float* __restrict__ dy, const float* __restr
   for (int j = 0; j < NT; ++j) xp[j * plane] += acc[j];
 }
 
+// ------------------------------------------- dense stride-2 convs as GEMMs
+// The dense convolutions of the blocks (3x3 stride 2 in the encoder, 4x4
+// stride-2 transposed in the decoder, pad 1, one group) and their input
+// gradients as tiled FP32 implicit GEMMs on the CUDA cores:
+//   ENC_FWD   y[b][n][Y][X]      = bias[n] + sum_{i,ky,kx} W[n][i][ky][kx] x[b][i][2Y-1+ky][2X-1+kx]
+//   DEC_FWD   y[b][n][2yo+py][2xo+px] = bias[n] + sum_{i,sy,sx} W[i][n][ky][kx] x[b][i][yo+py-sy][xo+px-sx],
+//             ky = 1 - py + 2 sy (the four taps of output phase (py, px))
+//   ENC_DGRAD dx[b][n][yy][xx]  += sum_{o,ky,kx} W[o][n][ky][kx] dy[b][o][(yy+1-ky)/2][(xx+1-kx)/2]
+//             over the taps of parity ky = yy + 1 (mod 2) (one or two per axis)
+//   DEC_DGRAD dx[b][n][yi][xi]  += sum_{o,ky,kx} W[n][o][ky][kx] dy[b][o][2yi-1+ky][2xi-1+kx]
+// GEMM rows m are pixels (of one output phase: blockIdx.z), columns n output
+// channels, K runs over (input channel, tap). A block computes BM x BN
+// outputs (4 x 4 per thread, BM * BN = 4096) in K-steps of 8 staged in shared
+// memory. Sums run in FP32 in increasing k.
+enum { ENC_FWD = 0, DEC_FWD = 1, ENC_DGRAD = 2, DEC_DGRAD = 3 };
+
+struct GemmArgs {
+  const float* src;   // x (forward) or dy (input gradient), NCHW
+  const float* w;     // the conv's weights in PyTorch layout
+  const float* bias;  // forward only, or null
+  float* out;         // y (written) or dx (accumulated)
+  int B, Cs, Hs, Ws;  // source tensor
+  int N, Ho, Wo;      // output channels and output map
+  int Cw;             // the weight tensor's other channel count
+};
+
+template <int CASE, int BN>
+__global__ void __launch_bounds__(256) k_igemm(GemmArgs a) {
+  constexpr int BM = 4096 / BN, BK = 8, KPT = BK * BM / 256;
+  __shared__ __align__(16) float As[BK][BM];
+  __shared__ __align__(16) float Bs[BK][BN];
+  const int tid = threadIdx.x, py = blockIdx.z >> 1, px = blockIdx.z & 1;
+  // phase grid of the GEMM rows: pixels (b, r, c) of an Hr x Wr map
+  int Hr, Wr, ty = 1, tx = 1, K;
+  if (CASE == ENC_FWD) { Hr = a.Ho; Wr = a.Wo; K = a.Cs * 9; }
+  else if (CASE == DEC_FWD) { Hr = a.Hs; Wr = a.Ws; K = a.Cs * 4; }
+  else if (CASE == ENC_DGRAD) { Hr = a.Ho / 2; Wr = a.Wo / 2; ty = py ? 2 : 1; tx = px ? 2 : 1; K = a.Cs * ty * tx; }
+  else { Hr = a.Ho; Wr = a.Wo; K = a.Cs * 16; }
+  const long M = (long)a.B * Hr * Wr;
+  const long m0 = (long)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  // this thread's A row and K slice for the tile loads
+  const int ml = tid % BM, kg = tid / BM;
+  const long mrow = m0 + ml;
+  const bool mok = mrow < M;
+  int bb = 0, rr = 0, cc = 0;
+  if (mok) {
+    bb = (int)(mrow / ((long)Hr * Wr));
+    const int q = (int)(mrow % ((long)Hr * Wr));
+    rr = q / Wr;
+    cc = q % Wr;
+  }
+  const int tn = tid % (BN / 4), tm = tid / (BN / 4);
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int kl = kg * KPT + j, k = k0 + kl;
+      float v = 0.f;
+      if (mok && k < K) {
+        if (CASE == ENC_FWD) {
+          const int i = k / 9, t = k % 9, y = 2 * rr - 1 + t / 3, x = 2 * cc - 1 + t % 3;
+          if (y >= 0 && y < a.Hs && x >= 0 && x < a.Ws) v = a.src[(((size_t)bb * a.Cs + i) * a.Hs + y) * a.Ws + x];
+        } else if (CASE == DEC_FWD) {
+          const int i = k >> 2, sy = (k >> 1) & 1, sx = k & 1, y = rr + py - sy, x = cc + px - sx;
+          if (y >= 0 && y < a.Hs && x >= 0 && x < a.Ws) v = a.src[(((size_t)bb * a.Cs + i) * a.Hs + y) * a.Ws + x];
+        } else if (CASE == ENC_DGRAD) {
+          const int o = k / (ty * tx), t = k % (ty * tx);
+          const int ky = py ? 2 * (t / tx) : 1, kx = px ? 2 * (t % tx) : 1;
+          const int y = (2 * rr + py + 1 - ky) / 2, x = (2 * cc + px + 1 - kx) / 2;
+          if (y >= 0 && y < a.Hs && x >= 0 && x < a.Ws) v = a.src[(((size_t)bb * a.Cs + o) * a.Hs + y) * a.Ws + x];
+        } else {
+          const int o = k >> 4, ky = (k >> 2) & 3, kx = k & 3, y = 2 * rr - 1 + ky, x = 2 * cc - 1 + kx;
+          if (y >= 0 && y < a.Hs && x >= 0 && x < a.Ws) v = a.src[(((size_t)bb * a.Cs + o) * a.Hs + y) * a.Ws + x];
+        }
+      }
+      As[kl][ml] = v;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kl = e / BN, nl = e % BN, k = k0 + kl, n = n0 + nl;
+      float v = 0.f;
+      if (k < K && n < a.N) {
+        if (CASE == ENC_FWD) {
+          v = a.w[(size_t)n * K + k];
+        } else if (CASE == DEC_FWD) {
+          const int i = k >> 2, sy = (k >> 1) & 1, sx = k & 1, ky = 1 - py + 2 * sy, kx = 1 - px + 2 * sx;
+          v = a.w[(((size_t)i * a.N + n) * 4 + ky) * 4 + kx];
+        } else if (CASE == ENC_DGRAD) {
+          const int o = k / (ty * tx), t = k % (ty * tx);
+          const int ky = py ? 2 * (t / tx) : 1, kx = px ? 2 * (t % tx) : 1;
+          v = a.w[(((size_t)o * a.N + n) * 3 + ky) * 3 + kx];
+        } else {
+          v = a.w[((size_t)n * a.Cs) * 16 + k];
+        }
+      }
+      Bs[kl][nl] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 av = *(const float4*)&As[kk][tm * 4];
+      const float4 bv = *(const float4*)&Bs[kk][tn * 4];
+      const float am[4] = {av.x, av.y, av.z, av.w}, bn[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += am[i] * bn[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long m = m0 + tm * 4 + i;
+    if (m >= M) continue;
+    const int b = (int)(m / ((long)Hr * Wr)), q = (int)(m % ((long)Hr * Wr)), r = q / Wr, c = q % Wr;
+    int Y = r, X = c;
+    if (CASE == DEC_FWD) { Y = 2 * r + py; X = 2 * c + px; }
+    if (CASE == ENC_DGRAD) { Y = 2 * r + py; X = 2 * c + px; }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tn * 4 + j;
+      if (n >= a.N) continue;
+      float* o = a.out + (((size_t)b * a.N + n) * a.Ho + Y) * a.Wo + X;
+      if (CASE == ENC_FWD || CASE == DEC_FWD)
+        *o = acc[i][j] + (a.bias ? a.bias[n] : 0.f);
+      else
+        *o += acc[i][j];
+    }
+  }
+}
+
 __device__ float block_sum(float v, float* sh) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -641,9 +776,33 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     else
       cudaMemcpyAsync(xin, a.in, sizeof(float) * B * 3 * n0, cudaMemcpyDeviceToDevice, st);
   }
+  // dense stride-2 convs (and their input gradients) as tiled GEMMs
+  auto igemm = [&](int cse, const float* src, const float* w, const float* bias, float* out, int Cs, int Hs,
+                   int Ws, int N, int Ho, int Wo) {
+    GemmArgs ga{src, w, bias, out, B, Cs, Hs, Ws, N, Ho, Wo, 0};
+    const long rows = cse == ENC_FWD ? (long)Ho * Wo
+                      : cse == DEC_FWD ? (long)Hs * Ws
+                      : cse == ENC_DGRAD ? (long)(Ho / 2) * (Wo / 2)
+                                         : (long)Ho * Wo;
+    const int bn = N >= 64 ? 64 : N >= 32 ? 32 : 16, bm = 4096 / bn;
+    dim3 grid(cdiv((long)B * rows, bm), cdiv(N, bn), (cse == DEC_FWD || cse == ENC_DGRAD) ? 4 : 1);
+    auto go = [&](auto kern) { kern<<<grid, 256, 0, st>>>(ga); };
+#define STDA_IGEMM(C)                                                  \
+  (bn == 64 ? go(k_igemm<C, 64>) : bn == 32 ? go(k_igemm<C, 32>) : go(k_igemm<C, 16>))
+    if (cse == ENC_FWD) STDA_IGEMM(ENC_FWD);
+    else if (cse == DEC_FWD) STDA_IGEMM(DEC_FWD);
+    else if (cse == ENC_DGRAD) STDA_IGEMM(ENC_DGRAD);
+    else STDA_IGEMM(DEC_DGRAD);
+#undef STDA_IGEMM
+  };
+  auto dense_s2 = [](int k, int s, int p, int g, bool tr) { return g == 1 && s == 2 && p == 1 && k == (tr ? 4 : 3); };
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
     if (!run) return;
+    if (dense_s2(k, s, p, g, tr)) {
+      igemm(tr ? DEC_FWD : ENC_FWD, x, w, bias, y, Ci, h, wd, Co, Ho, Wo);
+      return;
+    }
     const int nt = (Co / g) % 8 == 0 ? 8 : (Co / g) % 4 == 0 ? 4 : 1;
     long n = (long)B * (Co / nt) * Ho * Wo;
     auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo); };
@@ -762,6 +921,10 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
     if (!run) return;
+    if (dense_s2(k, s, p, g, tr)) {
+      igemm(tr ? DEC_DGRAD : ENC_DGRAD, dy, w, nullptr, dx, Co, Ho, Wo, Ci, hh, ww);
+      return;
+    }
     const int nt = (Ci / g) % 8 == 0 ? 8 : (Ci / g) % 4 == 0 ? 4 : 1;
     long n = (long)B * (Ci / nt) * hh * ww;
     auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo); };
