@@ -20,10 +20,44 @@ namespace stda {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kChunkWin = 4;  // windows per weight-gradient partial
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 inline dim3 grid1(long n) { return dim3(cdiv(n, kT)); }
+// grid of the per-plane elementwise kernels: x over the n pixels of a plane,
+// y over the planes (each block loops over planes y, y + gridDim.y, ...)
+inline dim3 gridp(long total, long n) { return dim3(cdiv(n, kT), (unsigned)std::min(total / n, 65535L)); }
+inline int planes(long total, long n) { return (int)(total / n); }
+
+// Reductions over the B windows' pixels are split into slices of at least
+// kMinSlice pixels, enough of them for about kSliceBlocks blocks per SM, the
+// partial sums of one launch holding at most kPartCap floats.
+constexpr int kMinSlice = 1024;
+constexpr int kSliceBlocks = 8;
+constexpr long kPartCap = 1L << 22;
+
+int device_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Slicing of `total` pixels for a launch of `width` blocks per slice whose
+// partials are `outputs` floats per slice: {pixels per slice, slices}.
+struct Slices {
+  int S, n;
+};
+Slices slices(long total, long width, long outputs, int align, int blocks_per_sm, int min_slice = kMinSlice) {
+  long want = ((long)device_sms() * blocks_per_sm + width - 1) / width;
+  want = std::max(1L, std::min(want, kPartCap / std::max(1L, outputs)));
+  long S = std::max((long)min_slice, (total + want - 1) / want);
+  S = (S + align - 1) / align * align;
+  return Slices{(int)S, (int)cdiv(total, S)};
+}
 
 // ----------------------------------------------------------- forward ops
 // Each thread computes NT consecutive output channels (forward) or input
@@ -37,11 +71,9 @@ template <int NT>
 __global__ void k_conv(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
                        float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
                        int Ho, int Wo) {
-  const int CoT = Co / NT;
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * CoT * Ho * Wo) return;
-  int X = idx % Wo, Y = (idx / Wo) % Ho, o0 = (int)((idx / ((long)Wo * Ho)) % CoT) * NT,
-      b = idx / ((long)Wo * Ho * CoT);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Ho * Wo) return;
+  const int Y = q / Wo, X = q - Y * Wo, o0 = blockIdx.y * NT, b = blockIdx.z;
   int cig = Ci / g, gi = o0 / (Co / g);
   float acc[NT];
 #pragma unroll
@@ -72,11 +104,9 @@ template <int NT>
 __global__ void k_convT(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
                         float* __restrict__ y, int B, int Ci, int H, int W, int Co, int k, int s, int p, int g,
                         int Ho, int Wo) {
-  const int CoT = Co / NT;
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * CoT * Ho * Wo) return;
-  int X = idx % Wo, Y = (idx / Wo) % Ho, o0 = (int)((idx / ((long)Wo * Ho)) % CoT) * NT,
-      b = idx / ((long)Wo * Ho * CoT);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Ho * Wo) return;
+  const int Y = q / Wo, X = q - Y * Wo, o0 = blockIdx.y * NT, b = blockIdx.z;
   int cig = Ci / g, cog = Co / g, gi = o0 / cog, ol0 = o0 % cog;
   float acc[NT];
 #pragma unroll
@@ -107,11 +137,9 @@ __global__ void k_convT(const float* __restrict__ x, const float* __restrict__ w
 template <int NT>
 __global__ void k_conv_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
                              int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
-  const int CiT = Ci / NT;
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * CiT * H * W) return;
-  int xx = idx % W, yy = (idx / W) % H, i0 = (int)((idx / ((long)W * H)) % CiT) * NT,
-      b = idx / ((long)W * H * CiT);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H * W) return;
+  const int yy = q / W, xx = q - yy * W, i0 = blockIdx.y * NT, b = blockIdx.z;
   int cig = Ci / g, cog = Co / g, gi = i0 / cig, il0 = i0 % cig;
   float acc[NT];
 #pragma unroll
@@ -142,11 +170,9 @@ __global__ void k_conv_dgrad(const float* __restrict__ dy, const float* __restri
 template <int NT>
 __global__ void k_convT_dgrad(const float* __restrict__ dy, const float* __restrict__ w, float* __restrict__ dx,
                               int B, int Ci, int H, int W, int Co, int k, int s, int p, int g, int Ho, int Wo) {
-  const int CiT = Ci / NT;
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)B * CiT * H * W) return;
-  int xi = idx % W, yi = (idx / W) % H, i0 = (int)((idx / ((long)W * H)) % CiT) * NT,
-      b = idx / ((long)W * H * CiT);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H * W) return;
+  const int yi = q / W, xi = q - yi * W, i0 = blockIdx.y * NT, b = blockIdx.z;
   int cig = Ci / g, cog = Co / g, gi = i0 / cig;
   float acc[NT];
 #pragma unroll
@@ -171,6 +197,134 @@ __global__ void k_convT_dgrad(const float* __restrict__ dy, const float* __restr
   float* xp = dx + ((size_t)b * Ci + i0) * plane + (size_t)yi * W + xi;
 #pragma unroll
   for (int j = 0; j < NT; ++j) xp[j * plane] += acc[j];
+}
+
+// ------------------------------------------ depthwise stride-1 convs
+// The per-channel (groups = channels) K x K convs of the blocks' first stage,
+// stride 1, pad P = (K - 1) / 2, and their transposed twins are one
+// correlation per channel, dst[c][Y][X] (+)= bias[c] + sum_{ky,kx}
+// src[c][Y + d ky - d P][X + d kx - d P] w[c][ky][kx] with d = +1, or d = -1
+// (FLIP) for the kernel flipped:
+//   conv forward, transposed-conv input gradient: d = +1
+//   transposed-conv forward, conv input gradient: d = -1
+// One thread per output pixel; grid (pixels / 256, C, B).
+template <int K, bool FLIP>
+__global__ void __launch_bounds__(256) k_dw(const float* __restrict__ src, const float* __restrict__ w,
+                                            const float* __restrict__ bias, float* __restrict__ dst, int C, int H,
+                                            int W, int accumulate) {
+  constexpr int P = (K - 1) / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H * W) return;
+  const int c = blockIdx.y, Y = q / W, X = q - Y * W;
+  const size_t plane = ((size_t)blockIdx.z * C + c) * H * W;
+  const float* sp = src + plane;
+  float wk[K * K];
+#pragma unroll
+  for (int t = 0; t < K * K; ++t) wk[t] = w[c * K * K + t];
+  float acc = bias ? bias[c] : 0.f;
+#pragma unroll
+  for (int ky = 0; ky < K; ++ky) {
+    const int sy = FLIP ? Y + P - ky : Y - P + ky;
+    if ((unsigned)sy >= (unsigned)H) continue;
+#pragma unroll
+    for (int kx = 0; kx < K; ++kx) {
+      const int sx = FLIP ? X + P - kx : X - P + kx;
+      if ((unsigned)sx < (unsigned)W) acc += sp[sy * W + sx] * wk[ky * K + kx];
+    }
+  }
+  float* dp = dst + plane + q;
+  *dp = accumulate ? *dp + acc : acc;
+}
+
+// Weight gradients of the stride-1, pad (K - 1) / 2 convs: the per-channel
+// ones (DW: dW[c][t] = sum_p A[c][p] G[c][p + t - P]) and the full ones of
+// few channels (dW[a][g][t] = sum_p A[a][p] G[g][p + t - P], A = dy with CA
+// output channels, G = x with CG input channels; index (a CG + g) K^2 + t).
+// For a conv A = dy and G = x; for a transposed depthwise conv A = x and
+// G = dy. A thread walks down L rows of one column X of one window, keeping
+// the K x K window of G (NG channels) in registers and loading one new G row
+// per step; it accumulates NA x NG x K^2 sums. Group blockIdx.y selects the
+// channels (DW: channel y; full: A channels (y / ngg) NA + a, G channels
+// (y % ngg) NG + j). Each block sums its threads (warp shuffles, then one
+// pass over the warps) into part[blockIdx.x][output index].
+template <int K, int NA, int NG, bool DW>
+__global__ void __launch_bounds__(256) k_wgrad_s1(const float* __restrict__ A, const float* __restrict__ G,
+                                                  float* __restrict__ part, int B, int H, int W, int CA, int CG,
+                                                  int L, int nseg, int nout) {
+  constexpr int P = (K - 1) / 2, KK = K * K, NV = NA * NG * KK;
+  __shared__ float sh[8][NV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = blockIdx.y, ngg = DW ? 1 : CG / NG;
+  const int a0 = DW ? grp : (grp / ngg) * NA, g0 = DW ? grp : (grp % ngg) * NG;
+  const int task = blockIdx.x * blockDim.x + tid;
+  float acc[NA][NG][KK];
+#pragma unroll
+  for (int i = 0; i < NA; ++i)
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+#pragma unroll
+      for (int t = 0; t < KK; ++t) acc[i][j][t] = 0.f;
+  if (task < B * nseg * W) {
+    const int X = task % W, r = task / W, yseg = r % nseg, b = r / nseg;
+    const int y0 = yseg * L, y1 = min(H, y0 + L);
+    const size_t plane = (size_t)H * W;
+    const float* ap = A + ((size_t)b * CA + a0) * plane + X;
+    const float* gp = G + ((size_t)b * (DW ? CA : CG) + g0) * plane;
+    float win[NG][K][K];  // win[j][ry][kx] = G[g0 + j][Y - P + ry][X - P + kx]
+    auto load_row = [&](int gy, int ry) {
+#pragma unroll
+      for (int j = 0; j < NG; ++j)
+#pragma unroll
+        for (int kx = 0; kx < K; ++kx) {
+          const int gx = X - P + kx;
+          win[j][ry][kx] = (unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W
+                               ? gp[j * plane + (size_t)gy * W + gx]
+                               : 0.f;
+        }
+    };
+#pragma unroll
+    for (int ry = 1; ry < K; ++ry) load_row(y0 - P + ry - 1, ry);
+    for (int Y = y0; Y < y1; ++Y) {
+#pragma unroll
+      for (int ry = 0; ry + 1 < K; ++ry)
+#pragma unroll
+        for (int j = 0; j < NG; ++j)
+#pragma unroll
+          for (int kx = 0; kx < K; ++kx) win[j][ry][kx] = win[j][ry + 1][kx];
+      load_row(Y + P, K - 1);
+      float av[NA];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) av[i] = ap[i * plane + (size_t)Y * W];
+#pragma unroll
+      for (int i = 0; i < NA; ++i)
+#pragma unroll
+        for (int j = 0; j < NG; ++j)
+#pragma unroll
+          for (int ry = 0; ry < K; ++ry)
+#pragma unroll
+            for (int kx = 0; kx < K; ++kx) acc[i][j][ry * K + kx] += av[i] * win[j][ry][kx];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NA; ++i)
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+#pragma unroll
+      for (int t = 0; t < KK; ++t) {
+        float v = acc[i][j][t];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[warp][(i * NG + j) * KK + t] = v;
+      }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int v = tid; v < NV; v += blockDim.x) {
+    float r = 0.f;
+    for (int k = 0; k < nw; ++k) r += sh[k][v];
+    const int i = v / (NG * KK), j = (v / KK) % NG, t = v % KK;
+    const int o = DW ? grp * KK + t : ((a0 + i) * CG + g0 + j) * KK + t;
+    part[(size_t)blockIdx.x * nout + o] = r;
+  }
 }
 
 // ------------------------------------------- dense stride-2 convs as GEMMs
@@ -308,6 +462,159 @@ __global__ void __launch_bounds__(256) k_igemm(GemmArgs a) {
   }
 }
 
+// Weight gradients of the full (one-group) convs as split-K FP32 GEMMs:
+//   conv:       dW[o][i][ky][kx] = sum_{b,Y,X} dy[b][o][Y][X] x[b][i][sY-p+ky][sX-p+kx]
+//   transposed: dW[i][o][ky][kx] = sum_{b,y,x} x[b][i][y][x] dy[b][o][sy-p+ky][sx-p+kx]
+// Both are part[slice][r][c] = sum over the slice's pixels m of A[m][r] G[m][c]:
+// A the row operand (dy of a conv, x of a transposed conv) on its own map
+// Hp x Wp, r its channel (M rows, padded with zero rows to MP, a multiple of
+// 4); G the gathered operand on its map Hg x Wg, c = channel * KS^2 + tap (N
+// columns). A block owns columns [n0, n0 + BN) of one slice (S pixels, a
+// multiple of 32) and stages 32 pixels at a time in shared memory, one row
+// or column per warp pass with lane = pixel, in 16-byte groups XOR-swizzled
+// by (row / 4) mod 8 so that the lane-per-pixel stores and the per-thread
+// 4 x 4 float4 reads are free of bank conflicts. The next stage's values are
+// loaded into registers while the current one is multiplied. KG groups of
+// P = (MP / 4) (BN / 4) threads take the 4-pixel groups of a stage in turn;
+// their 4 x 4 sums are added in group order at the end.
+struct WgArgs {
+  const float* a;  // row operand, [B][M][Hp][Wp]
+  const float* g;  // gathered operand, [B][CG][Hg][Wg]
+  float* part;     // [slices][M][N]
+  int B, M, MP, N, CG, Hp, Wp, Hg, Wg, s, p;
+  int BN, KG, S;
+};
+// values of one stage each lane loads: rows wq + i nw (i < kWgRows), columns
+// wq + j nw (j < kWgCols)
+constexpr int kWgRows = 8, kWgCols = 16;
+
+__device__ __forceinline__ int wg_swz(int row, int grp) { return row * 32 + ((grp ^ ((row >> 2) & 7)) << 2); }
+
+template <int KS>
+__global__ void __launch_bounds__(256, 3) k_wgemm(WgArgs a) {
+  constexpr int KK = KS * KS;
+  extern __shared__ __align__(16) float wsm[];
+  float* As = wsm;                 // [MP][32], swizzled
+  float* Gs = wsm + 32 * a.MP;     // [BN][32], swizzled
+  int* tab = (int*)(Gs + 32 * a.BN);
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wq = tid >> 5, nw = nth >> 5;
+  const int P = (a.MP >> 2) * (a.BN >> 2), kg = tid / P, pos = tid % P;
+  const int tm = pos / (a.BN >> 2), tn = pos % (a.BN >> 2);
+  const bool act = kg < a.KG;
+  const int n0 = blockIdx.y * a.BN;
+  const int np = a.Hp * a.Wp;
+  const int K = a.B * np, k0 = blockIdx.x * a.S, k1 = min(K, k0 + a.S);
+  const int gplane = a.Hg * a.Wg;
+  // column c: offset of its (channel, ky, kx) in a window of G << 4 | ky << 2 | kx
+  for (int c = tid; c < a.BN; c += nth) {
+    const int col = n0 + c, ch = col / KK, t = col % KK, ky = t / KS, kx = t % KS;
+    tab[c] = col < a.N ? ((ch * gplane + ky * a.Wg + kx) << 4) | (ky << 2) | kx : -1;
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float ra[kWgRows], rg[kWgCols];
+  auto fetch = [&](int s0) {
+    const int m = s0 + lane;
+    const bool mok = m < k1;
+    int b = 0, q = 0, Y = 0, X = 0;
+    if (mok) {
+      b = (unsigned)m / (unsigned)np;
+      q = m - b * np;
+      Y = (unsigned)q / (unsigned)a.Wp;
+      X = q - Y * a.Wp;
+    }
+    const float* ab = a.a + (size_t)b * a.M * np + q;
+#pragma unroll
+    for (int i = 0; i < kWgRows; ++i) {
+      const int r = wq + i * nw;
+      ra[i] = mok && r < a.M ? ab[(size_t)r * np] : 0.f;
+    }
+    const int gy0 = a.s * Y - a.p, gx0 = a.s * X - a.p;
+    const float* gb = a.g + (size_t)b * a.CG * gplane + (gy0 * a.Wg + gx0);
+#pragma unroll
+    for (int j = 0; j < kWgCols; ++j) {
+      const int c = wq + j * nw;
+      float v = 0.f;
+      if (mok && c < a.BN) {
+        const int e = tab[c];
+        if (e >= 0 && (unsigned)(gy0 + ((e >> 2) & 3)) < (unsigned)a.Hg && (unsigned)(gx0 + (e & 3)) < (unsigned)a.Wg)
+          v = gb[e >> 4];
+      }
+      rg[j] = v;
+    }
+  };
+  __syncthreads();  // the column table
+  if (k0 < k1) fetch(k0);
+  const int so = lane & 3, sg = lane >> 2;
+  for (int s0 = k0; s0 < k1; s0 += 32) {
+    __syncthreads();  // the previous stage's reads are done
+#pragma unroll
+    for (int i = 0; i < kWgRows; ++i) {
+      const int r = wq + i * nw;
+      if (r < a.MP) As[wg_swz(r, sg) + so] = ra[i];
+    }
+#pragma unroll
+    for (int j = 0; j < kWgCols; ++j) {
+      const int c = wq + j * nw;
+      if (c < a.BN) Gs[wg_swz(c, sg) + so] = rg[j];
+    }
+    __syncthreads();
+    if (s0 + 32 < k1) fetch(s0 + 32);
+    if (act) {
+      for (int grp = kg; grp < 8; grp += a.KG) {
+        float4 av[4], gv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = *(const float4*)&As[wg_swz(tm * 4 + i, grp)];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gv[j] = *(const float4*)&Gs[wg_swz(tn * 4 + j, grp)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] += av[i].x * gv[j].x;
+            acc[i][j] += av[i].y * gv[j].y;
+            acc[i][j] += av[i].z * gv[j].z;
+            acc[i][j] += av[i].w * gv[j].w;
+          }
+      }
+    }
+  }
+  // k-group sums, in group order: red[(kg * 16 + v) * P + pos]
+  if (a.KG > 1) {
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) wsm[(kg * 16 + i * 4 + j) * P + pos] = acc[i][j];
+    }
+    __syncthreads();
+    if (kg == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float r = wsm[(i * 4 + j) * P + pos];
+          for (int k = 1; k < a.KG; ++k) r += wsm[(k * 16 + i * 4 + j) * P + pos];
+          acc[i][j] = r;
+        }
+    }
+  }
+  if (kg == 0) {
+    float* out = a.part + (size_t)blockIdx.x * a.M * a.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int row = tm * 4 + i, col = n0 + tn * 4 + j;
+        if (row < a.M && col < a.N) out[(size_t)row * a.N + col] = acc[i][j];
+      }
+  }
+}
+
 __device__ float block_sum(float v, float* sh) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -322,20 +629,24 @@ __device__ float block_sum(float v, float* sh) {
 }
 
 // Weight gradient of NT channel pairs of a conv (or of a transposed conv
-// when TR) over the windows of one chunk: one block per pair tile, the
-// shared operand (dy of output o for a conv, x of input i for a transposed
-// conv) loaded once per pixel for the NT pairs; per value a warp shuffle
-// reduction, then one pass over the warps; part[chunk][pair * k * k + tap].
+// when TR) over one slice of the flattened (window, pixel) domain: pixels
+// [blockIdx.y S, blockIdx.y S + S) of the B n pixels (n = Ho Wo for a conv,
+// H W for a transposed conv). One block per pair tile, the shared operand
+// (dy of output o for a conv, x of input i for a transposed conv) loaded once
+// per pixel for the NT pairs; per value a warp shuffle reduction, then one
+// pass over the warps; part[slice][pair * k * k + tap].
 // K is the kernel size (1, 3 or 4) as a template argument, so the sums stay
 // in registers.
 template <bool TR, int K, int NT>
 __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ dy, float* __restrict__ part,
                         int B, int Ci, int H, int W, int Co, int s, int p, int g, int Ho, int Wo,
-                        int npairs) {
+                        int npairs, int S) {
   constexpr int k = K, KK = K * K, NV = NT * KK;
   __shared__ float sh[32 * NV];
   const int tile = blockIdx.x, chunk = blockIdx.y;
   const int cig = Ci / g, cog = Co / g;
+  const long npix = TR ? (long)H * W : (long)Ho * Wo;
+  const long e0 = (long)chunk * S, e1 = min((long)B * npix, e0 + S);
   int i, o, pair0;
   if (!TR) {  // pairs o * cig + il, il = il0 .. il0 + NT - 1
     o = tile / (cig / NT);
@@ -353,13 +664,13 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
   for (int j = 0; j < NT; ++j)
 #pragma unroll
     for (int t = 0; t < KK; ++t) acc[j][t] = 0.f;
-  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
   if (!TR) {
     const int n = Ho * Wo;
-    for (int b = b0; b < b1; ++b) {
+    for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
       const float* xp = x + ((size_t)b * Ci + i) * H * W;
       const float* dp = dy + ((size_t)b * Co + o) * n;
-      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         int Y = q / Wo, X = q % Wo;
         float d = dp[q];
 #pragma unroll
@@ -378,10 +689,11 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
     }
   } else {
     const int n = H * W;
-    for (int b = b0; b < b1; ++b) {
+    for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
       const float* xp = x + ((size_t)b * Ci + i) * n;
       const float* dp = dy + ((size_t)b * Co + o) * Ho * Wo;
-      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         int yi = q / W, xi = q % W;
         float v = xp[q];
 #pragma unroll
@@ -417,19 +729,21 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
   }
 }
 
-// Per-channel sums over one chunk of windows: S1 = sum a, S2 = sum a (v - mean) / sqrt(var + eps)
-// (S2 only if v); part[chunk][c][2].
+// Per-channel sums over one slice (pixels [chunk S, chunk S + S) of the B n):
+// S1 = sum a, S2 = sum a (v - mean) / sqrt(var + eps) (S2 only if v);
+// part[chunk][c][2].
 __global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict__ v, const float* __restrict__ mean,
-                            const float* __restrict__ var, float* __restrict__ part, int B, int C, int n) {
+                            const float* __restrict__ var, float* __restrict__ part, int B, int C, int n, int S) {
   __shared__ float sh[32];
   const int c = blockIdx.x, chunk = blockIdx.y;
-  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
+  const long e0 = (long)chunk * S, e1 = min((long)B * n, e0 + S);
   float s1 = 0.f, s2 = 0.f;
   float m = v ? mean[c] : 0.f, is = v ? rsqrtf(var[c] + 1e-5f) : 0.f;
-  for (int b = b0; b < b1; ++b) {
+  for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
     const float* ap = a + ((size_t)b * C + c) * n;
     const float* vp = v ? v + ((size_t)b * C + c) * n : nullptr;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
       float d = ap[q];
       s1 += d;
       if (vp) s2 += d * (vp[q] - m) * is;
@@ -443,15 +757,41 @@ __global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict
   }
 }
 
-// Sums partials over chunks in FP64 (fixed order) and adds them into the
-// gradient accumulator: acc[dst + j] += sum_chunk part[chunk][j * stride + off].
-__global__ void k_reduce(const float* __restrict__ part, int nchunks, int n, int stride, int off,
-                         double* __restrict__ acc, long dst) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// Sums partials over chunks in FP64 and adds them into the gradient
+// accumulator, acc[dst + j] += sum_chunk part[chunk][j * stride + off], or
+// (fout) writes fout[j] = scale * that sum. 256 threads: lane = output j of a
+// group of 32, warp w sums chunks w, w + 8, ...; the 8 warp sums are added in
+// warp order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ part, int nchunks, int n, int stride,
+                                                int off, double* __restrict__ acc, long dst,
+                                                float* __restrict__ fout, double scale) {
+  __shared__ double sh[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, j = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += (double)part[(size_t)c * n * stride + (size_t)j * stride + off];
-  acc[dst + j] += s;
+  if (j < n) {
+    const float* src = part + (size_t)j * stride + off;
+    const size_t cs = (size_t)n * stride;
+    int c = w;
+    for (; c + 24 < nchunks; c += 32) {
+      const float v0 = src[c * cs], v1 = src[(c + 8) * cs], v2 = src[(c + 16) * cs], v3 = src[(c + 24) * cs];
+      s += (double)v0;
+      s += (double)v1;
+      s += (double)v2;
+      s += (double)v3;
+    }
+    for (; c < nchunks; c += 8) s += (double)src[c * cs];
+  }
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && j < n) {
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r += sh[k][lane];
+    if (fout)
+      fout[j] = (float)(r * scale);
+    else
+      acc[dst + j] += r;
+  }
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, int n) {
@@ -462,12 +802,15 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, 
 // y = relu?(gam (x - mean) / sqrt(var + eps) + bet) per channel
 __global__ void k_bn(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ gam,
                      const float* __restrict__ bet, const float* __restrict__ mean, const float* __restrict__ var,
-                     long total, int C, int n, int relu) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  float v = gam[c] * (x[idx] - mean[c]) * rsqrtf(var[c] + 1e-5f) + bet[c];
-  y[idx] = relu ? fmaxf(v, 0.f) : v;
+                     int planes, int C, int n, int relu) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    const float v = gam[c] * (x[idx] - mean[c]) * rsqrtf(var[c] + 1e-5f) + bet[c];
+    y[idx] = relu ? fmaxf(v, 0.f) : v;
+  }
 }
 
 // stage 1: x1 = ReLU(BN1(t1) + BN2(t2) + BN3(x))
@@ -478,18 +821,24 @@ __device__ __forceinline__ float bnv(const BnP& q, int c, float x) {
   return q.g[c] * (x - q.m[c]) * rsqrtf(q.v[c] + 1e-5f) + q.b[c];
 }
 __global__ void k_stage1(const float* t1, const float* t2, const float* x, float* x1, BnP b1, BnP b2, BnP b3,
-                         long total, int C, int n) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  x1[idx] = fmaxf(bnv(b1, c, t1[idx]) + bnv(b2, c, t2[idx]) + bnv(b3, c, x[idx]), 0.f);
+                         int planes, int C, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    x1[idx] = fmaxf(bnv(b1, c, t1[idx]) + bnv(b2, c, t2[idx]) + bnv(b3, c, x[idx]), 0.f);
+  }
 }
 // y = ReLU(BN(u)) + r
-__global__ void k_stage2(const float* u, const float* r, float* y, BnP bn, long total, int C, int n) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  y[idx] = fmaxf(bnv(bn, c, u[idx]), 0.f) + r[idx];
+__global__ void k_stage2(const float* u, const float* r, float* y, BnP bn, int planes, int C, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    y[idx] = fmaxf(bnv(bn, c, u[idx]), 0.f) + r[idx];
+  }
 }
 
 // per (b, c): g = mean over the map
@@ -513,11 +862,14 @@ __global__ void k_eca_s(const float* g, const float* k3, float* sc, int B, int C
   sc[idx] = 1.f / (1.f + expf(-z));
 }
 // out = s * y (+ skip)
-__global__ void k_scale(const float* y, const float* sc, const float* skip, float* out, long total, int n) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  float v = sc[idx / n] * y[idx];
-  out[idx] = skip ? v + skip[idx] : v;
+__global__ void k_scale(const float* y, const float* sc, const float* skip, float* out, int planes, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const size_t idx = (size_t)pl * n + q;
+    const float v = sc[pl] * y[idx];
+    out[idx] = skip ? v + skip[idx] : v;
+  }
 }
 
 // output: z = sigmoid(logit); MSE gradient (or given gout) -> dlogit;
@@ -550,12 +902,19 @@ __global__ void k_out_loss(const float* logit, const float* target, const float*
     loss_part[blockIdx.x] = s;
   }
 }
-__global__ void k_sum_f64(const double* part, int n, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+// *out = sum of part[0 .. n), one block of 256 threads: thread t sums
+// t, t + 256, ... in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(256) k_sum_f64(const double* part, int n, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = sh[0];
 }
 
 // ---------------------------------------------------------- backward ops
@@ -590,38 +949,49 @@ __global__ void k_eca_back(const float* ds, const float* sc, const float* g, con
   for (int j = 0; j < 3; ++j) dk_part[b * 3 + j] = dk[j];
 }
 // dy = s * dout + dg (the mean's adjoint, already divided by n)
-__global__ void k_eca_dy(const float* dout, const float* sc, const float* dgm, float* dy, long total, int n) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  dy[idx] = sc[idx / n] * dout[idx] + dgm[idx / n];
+__global__ void k_eca_dy(const float* dout, const float* sc, const float* dgm, float* dy, int planes, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const size_t idx = (size_t)pl * n + q;
+    dy[idx] = sc[pl] * dout[idx] + dgm[pl];
+  }
 }
 // dbn = dy [BN(u) > 0]
-__global__ void k_relu_bn_mask(const float* dy, const float* u, BnP bn, float* dbn, long total, int C, int n) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  dbn[idx] = bnv(bn, c, u[idx]) > 0.f ? dy[idx] : 0.f;
+__global__ void k_relu_bn_mask(const float* dy, const float* u, BnP bn, float* dbn, int planes, int C, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    dbn[idx] = bnv(bn, c, u[idx]) > 0.f ? dy[idx] : 0.f;
+  }
 }
 // out (+)= a * gam / sqrt(var + eps)
-__global__ void k_bn_dx(const float* a, BnP bn, float* out, long total, int C, int n, int accumulate) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  float v = a[idx] * bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
-  out[idx] = accumulate ? out[idx] + v : v;
+__global__ void k_bn_dx(const float* a, BnP bn, float* out, int planes, int C, int n, int accumulate) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    const float v = a[idx] * bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
+    out[idx] = accumulate ? out[idx] + v : v;
+  }
 }
 // Batch statistics of a BN input x[B][C][n]: part[chunk][c] = sum over the
-// chunk's windows of x (mean == null) or of (x - mean[c])^2.
+// slice's pixels (chunk S .. chunk S + S of the B n) of x (mean == null) or
+// of (x - mean[c])^2.
 __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__ mean, float* __restrict__ part,
-                          int B, int C, int n) {
+                          int B, int C, int n, int S) {
   __shared__ float sh[32];
   const int c = blockIdx.x, chunk = blockIdx.y;
-  const int b0 = chunk * kChunkWin, b1 = min(B, b0 + kChunkWin);
+  const long e0 = (long)chunk * S, e1 = min((long)B * n, e0 + S);
   const float m = mean ? mean[c] : 0.f;
   float s = 0.f;
-  for (int b = b0; b < b1; ++b) {
+  for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
     const float* p = x + ((size_t)b * C + c) * n;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
       const float d = p[q] - m;
       s += mean ? d * d : p[q];
     }
@@ -629,25 +999,20 @@ __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__
   const float r = block_sum(s, sh);
   if (threadIdx.x == 0) part[(size_t)chunk * C + c] = r;
 }
-// out[c] = (sum over chunks of part[chunk][c]) / N, summed in FP64
-__global__ void k_bn_fin(const float* __restrict__ part, int nchunks, int C, double N, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  double s = 0.0;
-  for (int k = 0; k < nchunks; ++k) s += (double)part[(size_t)k * C + c];
-  out[c] = (float)(s / N);
-}
 // Batch-statistics BN adjoint: out (+)= gam / sigma (dy - (sum dy + xhat sum
 // dy xhat) / N), the two sums of this BN being gacc[dbet + c], gacc[dgam + c].
 __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const double* __restrict__ gacc, long dgam,
-                              long dbet, double N, float* out, long total, int C, int n, int accumulate) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  int c = (idx / n) % C;
-  const float is = rsqrtf(bn.v[c] + 1e-5f), xh = (x[idx] - bn.m[c]) * is;
-  const float corr = (float)((gacc[dbet + c] + (double)xh * gacc[dgam + c]) / N);
-  const float v = bn.g[c] * is * (dy[idx] - corr);
-  out[idx] = accumulate ? out[idx] + v : v;
+                              long dbet, double N, float* out, int planes, int C, int n, int accumulate) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int c = pl % C;
+    const size_t idx = (size_t)pl * n + q;
+    const float is = rsqrtf(bn.v[c] + 1e-5f), xh = (x[idx] - bn.m[c]) * is;
+    const float corr = (float)((gacc[dbet + c] + (double)xh * gacc[dgam + c]) / N);
+    const float v = bn.g[c] * is * (dy[idx] - corr);
+    out[idx] = accumulate ? out[idx] + v : v;
+  }
 }
 // dv = dx1 [x1 > 0]
 __global__ void k_relu_mask(const float* d, const float* act, float* out, long total) {
@@ -752,20 +1117,29 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   const size_t n0 = (size_t)H * W;
   cudaStream_t st = a.stream;
   const float* P = a.params;
-  const int nchunk = cdiv(B, kChunkWin);
+  // per-slice partial sums of the reductions (weight gradients, channel
+  // sums, batch statistics), one launch at a time
+  float* part = ar.f(kPartCap);
+  double* gacc = ar.d(kNumParams);  // gradient accumulator
+  // adds sum_chunk part[chunk][j * stride + off] to gacc[dst + j] (fout:
+  // writes fout[j] = scale * that sum)
+  auto reduce = [&](const float* pp, int nch, int n, int stride, int off, long dst, float* fout = nullptr,
+                    double scale = 1.0) {
+    k_reduce<<<cdiv(n, 32), 256, 0, st>>>(pp, nch, n, stride, off, gacc, dst, fout, scale);
+  };
   // BN statistics: the running ones, or (training mode) the batch's, computed
   // into `bst` (same layout as the running buffers) right before each BN
   float* bst = ar.f(kNumBuffers);
-  float* spart = ar.f((size_t)64 * nchunk);
   const float* Q = a.bn_batch ? bst : a.buffers;
   auto bnp = [&](int g, int b, int m, int v) { return BnP{P + g, P + b, Q + m, Q + v}; };
   auto batch_stats = [&](const float* x, int Cc, int n, int moff, int voff) {
     if (!run || !a.bn_batch) return;
     const double N = (double)B * n;
-    k_bn_part<<<dim3(Cc, nchunk), kT, 0, st>>>(x, nullptr, spart, B, Cc, n);
-    k_bn_fin<<<cdiv(Cc, kT), kT, 0, st>>>(spart, nchunk, Cc, N, bst + moff);
-    k_bn_part<<<dim3(Cc, nchunk), kT, 0, st>>>(x, bst + moff, spart, B, Cc, n);
-    k_bn_fin<<<cdiv(Cc, kT), kT, 0, st>>>(spart, nchunk, Cc, N, bst + voff);
+    const Slices sl = slices((long)B * n, Cc, Cc, 1, kSliceBlocks);
+    k_bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, nullptr, part, B, Cc, n, sl.S);
+    reduce(part, sl.n, Cc, 1, 0, 0, bst + moff, 1.0 / N);
+    k_bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, bst + moff, part, B, Cc, n, sl.S);
+    reduce(part, sl.n, Cc, 1, 0, 0, bst + voff, 1.0 / N);
   };
 
   // ---- forward with tape
@@ -803,9 +1177,19 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       igemm(tr ? DEC_FWD : ENC_FWD, x, w, bias, y, Ci, h, wd, Co, Ho, Wo);
       return;
     }
+    if (g == Ci && g == Co && s == 1 && p == (k - 1) / 2 && (k == 1 || k == 3)) {
+      const dim3 grid(cdiv((long)h * wd, kT), Ci, B);
+      if (k == 1)
+        k_dw<1, false><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+      else if (tr)
+        k_dw<3, true><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+      else
+        k_dw<3, false><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+      return;
+    }
     const int nt = (Co / g) % 8 == 0 ? 8 : (Co / g) % 4 == 0 ? 4 : 1;
-    long n = (long)B * (Co / nt) * Ho * Wo;
-    auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo); };
+    const dim3 grid(cdiv((long)Ho * Wo, kT), Co / nt, B);
+    auto go = [&](auto kern) { kern<<<grid, kT, 0, st>>>(x, w, bias, y, B, Ci, h, wd, Co, k, s, p, g, Ho, Wo); };
     if (tr)
       nt == 8 ? go(k_convT<8>) : nt == 4 ? go(k_convT<4>) : go(k_convT<1>);
     else
@@ -817,7 +1201,8 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   batch_stats(su, 8, (int)n0, C.stem_m, C.stem_v);
   if (run) {
     long n = (long)B * 8 * n0;
-    k_bn<<<grid1(n), kT, 0, st>>>(su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v, n, 8, (int)n0, 1);
+    k_bn<<<gridp(n, n0), kT, 0, st>>>(su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v, planes(n, n0),
+                                      8, (int)n0, 1);
   }
   BlkTape T[6];
   const float* cur = a0;
@@ -847,10 +1232,9 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     batch_stats(t.t2, ci, (int)n, C.m2[b], C.v2[b]);
     batch_stats(t.x, ci, (int)n, C.m3[b], C.v3[b]);
     if (run)
-      k_stage1<<<grid1((long)B * ci * n), kT, 0, st>>>(t.t1, t.t2, t.x, t.x1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]),
-                                                     bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
-                                                     bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), (long)B * ci * n, ci,
-                                                     (int)n);
+      k_stage1<<<gridp((long)B * ci * n, n), kT, 0, st>>>(
+          t.t1, t.t2, t.x, t.x1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
+          bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), B * ci, ci, (int)n);
     if (enc) {
       conv(t.x1, P + C.w2[b], nullptr, t.u, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
       conv(t.x, P + C.rw[b], P + C.rb[b], t.r, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
@@ -861,11 +1245,12 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     batch_stats(t.u, co, (int)n2, C.m[b], C.v[b]);
     if (run) {
       long tot = (long)B * co * n2;
-      k_stage2<<<grid1(tot), kT, 0, st>>>(t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), tot, co, (int)n2);
+      k_stage2<<<gridp(tot, n2), kT, 0, st>>>(t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), planes(tot, n2), co,
+                                              (int)n2);
       k_gap<<<B * co, kT, 0, st>>>(t.y, t.g, (int)n2);
       k_eca_s<<<cdiv(B * co, kT), kT, 0, st>>>(t.g, P + C.eca[b], t.s, B, co);
       const float* skip = b == 3 ? T[1].out : b == 4 ? T[0].out : nullptr;
-      k_scale<<<grid1(tot), kT, 0, st>>>(t.y, t.s, skip, t.out, tot, (int)n2);
+      k_scale<<<gridp(tot, n2), kT, 0, st>>>(t.y, t.s, skip, t.out, planes(tot, n2), (int)n2);
     }
     cur = t.out;
     h = t.H2;
@@ -879,32 +1264,93 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   conv(cur, P + C.out_w, P + C.out_b, logit, 8, H, W, 1, 3, 1, 1, 1, false, H, W);
   if (run) {
     k_out_loss<<<nlb, kT, 0, st>>>(logit, a.target, a.gout, z, dlogit, lpart, (long)B * n0, 1.0 / ((double)B * n0));
-    if (a.loss) k_sum_f64<<<1, 32, 0, st>>>(lpart, nlb, a.loss);
+    if (a.loss) k_sum_f64<<<1, 256, 0, st>>>(lpart, nlb, a.loss);
     if (a.z_out) cudaMemcpyAsync(a.z_out, z, sizeof(float) * B * n0, cudaMemcpyDeviceToDevice, st);
   }
 
   // ---- backward
-  double* gacc = ar.d(kNumParams);
   if (run) cudaMemsetAsync(gacc, 0, sizeof(double) * kNumParams, st);
-  // largest partial buffer: pairs * k * k per chunk
-  size_t part_max = 0;
-  for (int b = 0; b < 6; ++b) {
-    size_t dense = (size_t)(kBlkEnc[b] ? 9 : 16) * kBlkCin[b] * kBlkCout[b];
-    part_max = std::max(part_max, dense);
-  }
-  part_max = std::max(part_max, (size_t)216);
-  float* part = ar.f(part_max * nchunk);
   auto wgrad = [&](const float* x, const float* dy, int Ci, int hh, int ww, int Co, int k, int s, int p, int g,
                    bool tr, int Ho, int Wo, int dst) {
     if (!run) return;
+    // stride-1 convs: depthwise ones, and full ones of few channels (stem,
+    // output conv), by column walks with a register window
+    const bool dw = g == Ci && g == Co && s == 1 && p == (k - 1) / 2 && (k == 1 || k == 3);
+    const bool full3 = g == 1 && s == 1 && k == 3 && p == 1 && !tr && ((Ci == 3 && Co % 2 == 0) || Ci % 4 == 0);
+    if (dw || full3) {
+      const int groups = dw ? Ci : Ci == 3 ? Co / 2 : Co * (Ci / 4);
+      const long cols = (long)B * ww;
+      const long target = (long)device_sms() * 4 * 256 / groups;
+      int nseg = (int)std::max(1L, std::min((target + cols - 1) / cols, (long)std::max(1, hh / 8)));
+      const int L = cdiv(hh, nseg);
+      nseg = cdiv(hh, L);
+      const dim3 grid(cdiv(cols * nseg, 256), groups);
+      const int nout = (dw ? Ci : Ci * Co) * k * k;
+      if ((long)grid.x * nout <= kPartCap) {
+        const float* A = tr ? x : dy;
+        const float* G = tr ? dy : x;
+        if (dw && k == 1)
+          k_wgrad_s1<1, 1, 1, true><<<grid, 256, 0, st>>>(A, G, part, B, hh, ww, Ci, Ci, L, nseg, nout);
+        else if (dw)
+          k_wgrad_s1<3, 1, 1, true><<<grid, 256, 0, st>>>(A, G, part, B, hh, ww, Ci, Ci, L, nseg, nout);
+        else if (Ci == 3)
+          k_wgrad_s1<3, 2, 3, false><<<grid, 256, 0, st>>>(dy, x, part, B, hh, ww, Co, Ci, L, nseg, nout);
+        else
+          k_wgrad_s1<3, 1, 4, false><<<grid, 256, 0, st>>>(dy, x, part, B, hh, ww, Co, Ci, L, nseg, nout);
+        reduce(part, grid.x, nout, 1, 0, dst);
+        return;
+      }
+    }
+    if (g == 1 && (k == 3 || k == 4)) {
+      WgArgs wa;
+      wa.a = tr ? x : dy;
+      wa.g = tr ? dy : x;
+      wa.part = part;
+      wa.B = B;
+      wa.M = tr ? Ci : Co;
+      wa.MP = cdiv(wa.M, 4) * 4;
+      wa.CG = tr ? Co : Ci;
+      wa.N = wa.CG * k * k;
+      wa.Hp = tr ? hh : Ho;
+      wa.Wp = tr ? ww : Wo;
+      wa.Hg = tr ? Ho : hh;
+      wa.Wg = tr ? Wo : ww;
+      wa.s = s;
+      wa.p = p;
+      // column tiles of at most 4096 / MP columns (<= 256 threads of 4 x 4)
+      int nt = cdiv((long)wa.MP * wa.N, 4096);
+      wa.BN = cdiv(cdiv(wa.N, nt), 4) * 4;
+      while ((wa.MP / 4) * (wa.BN / 4) > 256) wa.BN = cdiv(cdiv(wa.N, ++nt), 4) * 4;
+      nt = cdiv(wa.N, wa.BN);
+      const int P = (wa.MP / 4) * (wa.BN / 4);
+      wa.KG = std::min(8, 256 / P);
+      const int threads = cdiv((long)P * wa.KG, 32) * 32, nw = threads / 32;
+      if (wa.MP <= kWgRows * nw && wa.BN <= kWgCols * nw && (long)B * wa.Hp * wa.Wp < (1L << 30) &&
+          (long)wa.CG * wa.Hg * wa.Wg < (1L << 27)) {
+        const Slices sl = slices((long)B * wa.Hp * wa.Wp, nt, (long)wa.M * wa.N, 32, 4, 256);
+        wa.S = sl.S;
+        const size_t smem = std::max(sizeof(float) * (32 * (wa.MP + wa.BN) + wa.BN),
+                                     wa.KG > 1 ? sizeof(float) * 16 * P * wa.KG : (size_t)0);
+        if (k == 3)
+          k_wgemm<3><<<dim3(sl.n, nt), threads, smem, st>>>(wa);
+        else
+          k_wgemm<4><<<dim3(sl.n, nt), threads, smem, st>>>(wa);
+        reduce(part, sl.n, wa.M * wa.N, 1, 0, dst);
+        return;
+      }
+    }
     int npairs = tr ? Ci * (Co / g) : Co * (Ci / g);
     // pairs per block: 4 where the tiled dimension (Ci / g for a conv,
     // Co / g for a transposed conv) allows
     // (2 for the 4x4 kernels, whose 16 sums per pair cost registers)
     const int tdim = tr ? Co / g : Ci / g;
     const int nt = tdim % 4 == 0 ? (k == 4 ? 2 : 4) : 1;
-    dim3 grid(npairs / nt, nchunk);
-    auto go = [&](auto kern) { kern<<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, s, p, g, Ho, Wo, npairs); };
+    const Slices sl = slices((long)B * (tr ? (long)hh * ww : (long)Ho * Wo), npairs / nt, (long)npairs * k * k, 1,
+                             kSliceBlocks);
+    dim3 grid(npairs / nt, sl.n);
+    auto go = [&](auto kern) {
+      kern<<<grid, kT, 0, st>>>(x, dy, part, B, Ci, hh, ww, Co, s, p, g, Ho, Wo, npairs, sl.S);
+    };
     if (nt == 4) {
       if (k == 1) tr ? go(k_wgrad<true, 1, 4>) : go(k_wgrad<false, 1, 4>);
       else tr ? go(k_wgrad<true, 3, 4>) : go(k_wgrad<false, 3, 4>);
@@ -915,8 +1361,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       else if (k == 3) tr ? go(k_wgrad<true, 3, 1>) : go(k_wgrad<false, 3, 1>);
       else tr ? go(k_wgrad<true, 4, 1>) : go(k_wgrad<false, 4, 1>);
     }
-    int n = npairs * k * k;
-    k_reduce<<<cdiv(n, kT), kT, 0, st>>>(part, nchunk, n, 1, 0, gacc, dst);
+    reduce(part, sl.n, npairs * k * k, 1, 0, dst);
   };
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
@@ -925,9 +1370,19 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       igemm(tr ? DEC_DGRAD : ENC_DGRAD, dy, w, nullptr, dx, Co, Ho, Wo, Ci, hh, ww);
       return;
     }
+    if (g == Ci && g == Co && s == 1 && p == (k - 1) / 2 && (k == 1 || k == 3)) {
+      const dim3 grid(cdiv((long)hh * ww, kT), Ci, B);
+      if (k == 1)
+        k_dw<1, false><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+      else if (tr)
+        k_dw<3, false><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+      else
+        k_dw<3, true><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+      return;
+    }
     const int nt = (Ci / g) % 8 == 0 ? 8 : (Ci / g) % 4 == 0 ? 4 : 1;
-    long n = (long)B * (Ci / nt) * hh * ww;
-    auto go = [&](auto kern) { kern<<<grid1(n), kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo); };
+    const dim3 grid(cdiv((long)hh * ww, kT), Ci / nt, B);
+    auto go = [&](auto kern) { kern<<<grid, kT, 0, st>>>(dy, w, dx, B, Ci, hh, ww, Co, k, s, p, g, Ho, Wo); };
     if (tr)
       nt == 8 ? go(k_convT_dgrad<8>) : nt == 4 ? go(k_convT_dgrad<4>) : go(k_convT_dgrad<1>);
     else
@@ -937,9 +1392,10 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto chan = [&](const float* av, const float* v, const float* mean, const float* var, int Cc, int n,
                   int dgam, int dbet) {
     if (!run) return;
-    k_chan_sums<<<dim3(Cc, nchunk), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n);
-    if (dbet >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 0, gacc, dbet);
-    if (dgam >= 0) k_reduce<<<cdiv(Cc, kT), kT, 0, st>>>(part, nchunk, Cc, 2, 1, gacc, dgam);
+    const Slices sl = slices((long)B * n, Cc, 2L * Cc, 1, kSliceBlocks);
+    k_chan_sums<<<dim3(Cc, sl.n), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n, sl.S);
+    if (dbet >= 0) reduce(part, sl.n, Cc, 2, 0, dbet);
+    if (dgam >= 0) reduce(part, sl.n, Cc, 2, 1, dgam);
   };
   // out (+)= dBN input: gam / sigma dy (running statistics), or the batch
   // adjoint, whose sums of this BN chan() has just added to gacc
@@ -947,10 +1403,10 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
                    int accumulate) {
     if (!run) return;
     if (a.bn_batch)
-      k_bn_dx_batch<<<grid1(tot), kT, 0, st>>>(d, x, bn, gacc, dgam, dbet, (double)B * n, out, tot, Cc, n,
+      k_bn_dx_batch<<<gridp(tot, n), kT, 0, st>>>(d, x, bn, gacc, dgam, dbet, (double)B * n, out, planes(tot, n), Cc, n,
                                                accumulate);
     else
-      k_bn_dx<<<grid1(tot), kT, 0, st>>>(d, bn, out, tot, Cc, n, accumulate);
+      k_bn_dx<<<gridp(tot, n), kT, 0, st>>>(d, bn, out, planes(tot, n), Cc, n, accumulate);
   };
   // output conv
   float* dcur = ar.f((size_t)B * 8 * n0);
@@ -989,11 +1445,11 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       // ECA
       k_eca_ds<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
       k_eca_back<<<cdiv(B, 64), 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
-      k_reduce<<<1, 32, 0, st>>>(dkp, B, 3, 1, 0, gacc, C.eca[b]);
-      k_eca_dy<<<grid1(tot2), kT, 0, st>>>(dcur, t.s, dgm, dy, tot2, n2);
+      reduce(dkp, B, 3, 1, 0, C.eca[b]);
+      k_eca_dy<<<gridp(tot2, n2), kT, 0, st>>>(dcur, t.s, dgm, dy, planes(tot2, n2), n2);
       // main branch: dbn = dy [BN(u) > 0]; du = dbn gam / sigma
       BnP bn = bnp(C.g[b], C.be[b], C.m[b], C.v[b]);
-      k_relu_bn_mask<<<grid1(tot2), kT, 0, st>>>(dy, t.u, bn, dtmp, tot2, co, n2);
+      k_relu_bn_mask<<<gridp(tot2, n2), kT, 0, st>>>(dy, t.u, bn, dtmp, planes(tot2, n2), co, n2);
     }
     chan(dtmp, t.u, Q + C.m[b], Q + C.v[b], co, n2, C.g[b], C.be[b]);
     bn_dx(dtmp, t.u, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), C.g[b], C.be[b], dtmp, tot2, co, n2, 0);
