@@ -327,6 +327,243 @@ __global__ void __launch_bounds__(256) k_wgrad_s1(const float* __restrict__ A, c
   }
 }
 
+// ------------------------------------- dense stride-2 convs, direct form
+// The dense (one-group) stride-2, pad-1 convs of the blocks and their input
+// gradients, as direct convolutions with the source tile staged in shared
+// memory (kDcMC channels a stage, with the K x K weights of the block's
+// output channels), each thread holding NP pixels x NO output channels:
+//   k_sconv  (conv, K = 3 encoder forward, K = 4 decoder input gradient):
+//     out[n][Y][X] (+)= bias[n] + sum_{m,ky,kx} w[n][m][ky][kx] src[m][2Y-1+ky][2X-1+kx]
+//   k_stconv (transposed, K = 4 decoder forward, K = 3 encoder input gradient):
+//     out[n][Y][X] (+)= bias[n] + sum w[m][n][ky][kx] src[m][yi][xi] over Y = 2yi-1+ky, X = 2xi-1+kx
+// Stages are copied with cp.async (zero-filled outside the source) into two
+// shared-memory buffers, the next stage in flight while the current one is
+// used. 256 threads: warp w = (row group or output phase, channel group);
+// lane = (row in the warp, column), TX columns per warp row. Sums run in FP32
+// over m, then ky, kx.
+constexpr int kDcMC = 4;  // source channels per stage
+
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int NO>
+__device__ __forceinline__ void load_w(const float* p, float (&wv)[NO]) {
+#pragma unroll
+  for (int q = 0; q < NO / 4; ++q) {
+    const float4 f = *(const float4*)&p[4 * q];
+    wv[4 * q] = f.x;
+    wv[4 * q + 1] = f.y;
+    wv[4 * q + 2] = f.z;
+    wv[4 * q + 3] = f.w;
+  }
+}
+
+template <int K, int NO, int TX>
+struct SconvGeo {
+  static constexpr int KK = K * K, RW = 32 / TX, NP = 2, TY = 4 * NP * RW, R = 2 * TY + K - 2;
+  static constexpr int PW = TX == 32 ? 33 : 20;  // parity-plane row (TX + 1, padded against conflicts)
+  static constexpr int RS = 2 * PW, CS = R * RS, NB = 2 * NO;
+  static constexpr int NX = kDcMC * CS, NW = kDcMC * KK * NB, STAGE = NX + NW;
+  static constexpr size_t smem() { return sizeof(float) * 2 * STAGE; }
+};
+
+template <int K, int NO, int TX>
+__global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, const float* __restrict__ w,
+                                               const float* __restrict__ bias, float* __restrict__ out, int M,
+                                               int Hs, int Ws, int N, int accumulate) {
+  using G = SconvGeo<K, NO, TX>;
+  constexpr int KK = G::KK, RW = G::RW, NP = G::NP, TY = G::TY, R = G::R, PW = G::PW, RS = G::RS, CS = G::CS;
+  constexpr int NB = G::NB;
+  extern __shared__ __align__(16) float dsm[];
+  const int Ho = Hs / 2, Wo = Ws / 2;
+  const int tilesx = (Wo + TX - 1) / TX;
+  const int X0 = (blockIdx.x % tilesx) * TX, Y0 = (blockIdx.x / tilesx) * TY;
+  const int n0 = blockIdx.y * NB, b = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5, cg = wq & 1, rg = wq >> 1;
+  const int x = lane % TX, ry = lane / TX;
+  const size_t splane = (size_t)Hs * Ws;
+  const float* sb = src + (size_t)b * M * splane;
+  auto issue = [&](int m0, float* buf) {
+    for (int e = tid; e < kDcMC * R * 2 * PW; e += 256) {
+      const int m = e / (R * 2 * PW), r = (e / (2 * PW)) % R, u = e % (2 * PW);
+      const int gy = 2 * Y0 - 1 + r, gx = 2 * X0 - 1 + u;
+      const bool ok = m0 + m < M && (unsigned)gy < (unsigned)Hs && (unsigned)gx < (unsigned)Ws && u < 2 * TX + K - 2;
+      cp_async4(buf + m * CS + r * RS + (u & 1) * PW + (u >> 1),
+                ok ? sb + (size_t)(m0 + m) * splane + (size_t)gy * Ws + gx : src, ok);
+    }
+    float* wsb = buf + G::NX;
+    for (int e = tid; e < G::NW; e += 256) {
+      const int nl = e % NB, t = (e / NB) % KK, m = e / (NB * KK), n = n0 + nl;
+      const bool ok = n < N && m0 + m < M;
+      cp_async4(wsb + e, ok ? w + ((size_t)n * M + m0 + m) * KK + t : w, ok);
+    }
+    cp_async_commit();
+  };
+  float acc[NP][NO];
+#pragma unroll
+  for (int i = 0; i < NP; ++i)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) acc[i][j] = 0.f;
+  issue(0, dsm);
+  int stage = 0;
+  for (int m0 = 0; m0 < M; m0 += kDcMC, ++stage) {
+    const float* xs = dsm + (stage & 1) * G::STAGE;
+    const float* ws = xs + G::NX;
+    if (m0 + kDcMC < M) {
+      issue(m0 + kDcMC, dsm + ((stage + 1) & 1) * G::STAGE);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* xb = xs + (2 * (rg * NP * RW + ry)) * RS + x;
+#pragma unroll
+    for (int m = 0; m < kDcMC; ++m) {
+#pragma unroll
+      for (int ky = 0; ky < K; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < K; ++kx) {
+          float wv[NO];
+          load_w<NO>(ws + (m * KK + ky * K + kx) * NB + cg * NO, wv);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            const float xv = xb[m * CS + (2 * i * RW + ky) * RS + (kx & 1) * PW + (kx >> 1)];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) acc[i][j] += xv * wv[j];
+          }
+        }
+    }
+    __syncthreads();  // this buffer is refilled two stages on
+  }
+  const size_t oplane = (size_t)Ho * Wo;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const int Y = Y0 + (rg * NP + i) * RW + ry, X = X0 + x;
+    if (Y >= Ho || X >= Wo) continue;
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      const int n = n0 + cg * NO + j;
+      if (n >= N) continue;
+      float* o = out + ((size_t)b * N + n) * oplane + (size_t)Y * Wo + X;
+      *o = accumulate ? *o + acc[i][j] : acc[i][j] + (bias ? bias[n] : 0.f);
+    }
+  }
+}
+
+template <int K, int NO, int TX>
+struct StconvGeo {
+  static constexpr int KK = K * K, RW = 32 / TX, NP = 2, TU = NP * RW, R = TU + 2;
+  static constexpr int RS = TX == 32 ? 34 : 48;  // source tile row (TX + 2, padded against conflicts)
+  static constexpr int CS = R * RS, NB = 2 * NO;
+  static constexpr int NX = kDcMC * CS, NW = kDcMC * KK * NB, STAGE = NX + NW;
+  static constexpr size_t smem() { return sizeof(float) * 2 * STAGE; }
+};
+
+// the taps of output phase (PY, PX) of k_stconv: ky = ky0 + 2 sy < K with
+// ky0 = (PY + 1) mod 2, source row offset (PY + 1 - ky) / 2 (likewise x)
+template <int K, int NO, int TX, int PY, int PX>
+__device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, float (&acc)[2][NO]) {
+  using G = StconvGeo<K, NO, TX>;
+  constexpr int KY0 = (PY + 1) & 1, KX0 = (PX + 1) & 1;
+  constexpr int NTY = KY0 + 2 < K ? 2 : 1, NTX = KX0 + 2 < K ? 2 : 1;
+#pragma unroll
+  for (int m = 0; m < kDcMC; ++m)
+#pragma unroll
+    for (int sy = 0; sy < NTY; ++sy)
+#pragma unroll
+      for (int sx = 0; sx < NTX; ++sx) {
+        const int ky = KY0 + 2 * sy, kx = KX0 + 2 * sx;
+        const int dy = (PY + 1 - ky) / 2, dx = (PX + 1 - kx) / 2;
+        float wv[NO];
+        load_w<NO>(wb + (m * G::KK + ky * K + kx) * G::NB, wv);
+#pragma unroll
+        for (int i = 0; i < G::NP; ++i) {
+          const float xv = xb[m * G::CS + (i * G::RW + 1 + dy) * G::RS + 1 + dx];
+#pragma unroll
+          for (int j = 0; j < NO; ++j) acc[i][j] += xv * wv[j];
+        }
+      }
+}
+
+template <int K, int NO, int TX>
+__global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, const float* __restrict__ w,
+                                                const float* __restrict__ bias, float* __restrict__ out, int M,
+                                                int Hs, int Ws, int N, int accumulate) {
+  using G = StconvGeo<K, NO, TX>;
+  constexpr int KK = G::KK, RW = G::RW, NP = G::NP, TU = G::TU, R = G::R, RS = G::RS, NB = G::NB;
+  extern __shared__ __align__(16) float dsm[];
+  const int Ho = 2 * Hs, Wo = 2 * Ws;
+  const int tilesx = (Ws + TX - 1) / TX;
+  const int V0 = (blockIdx.x % tilesx) * TX, U0 = (blockIdx.x / tilesx) * TU;
+  const int n0 = blockIdx.y * NB, b = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5, ph = wq & 3, cg = wq >> 2;
+  const int py = ph >> 1, px = ph & 1, v = lane % TX, ru = lane / TX;
+  const size_t splane = (size_t)Hs * Ws;
+  const float* sb = src + (size_t)b * M * splane;
+  auto issue = [&](int m0, float* buf) {
+    for (int e = tid; e < G::NX; e += 256) {
+      const int m = e / (R * RS), r = (e / RS) % R, c = e % RS;
+      const int gy = U0 - 1 + r, gx = V0 - 1 + c;
+      const bool ok = m0 + m < M && c < TX + 2 && (unsigned)gy < (unsigned)Hs && (unsigned)gx < (unsigned)Ws;
+      cp_async4(buf + e, ok ? sb + (size_t)(m0 + m) * splane + (size_t)gy * Ws + gx : src, ok);
+    }
+    float* wsb = buf + G::NX;
+    for (int e = tid; e < G::NW; e += 256) {
+      const int nl = e % NB, t = (e / NB) % KK, m = e / (NB * KK), n = n0 + nl;
+      const bool ok = n < N && m0 + m < M;
+      cp_async4(wsb + e, ok ? w + ((size_t)(m0 + m) * N + n) * KK + t : w, ok);
+    }
+    cp_async_commit();
+  };
+  float acc[NP][NO];
+#pragma unroll
+  for (int i = 0; i < NP; ++i)
+#pragma unroll
+    for (int j = 0; j < NO; ++j) acc[i][j] = 0.f;
+  issue(0, dsm);
+  int stage = 0;
+  for (int m0 = 0; m0 < M; m0 += kDcMC, ++stage) {
+    const float* xs = dsm + (stage & 1) * G::STAGE;
+    const float* ws = xs + G::NX;
+    if (m0 + kDcMC < M) {
+      issue(m0 + kDcMC, dsm + ((stage + 1) & 1) * G::STAGE);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* xb = xs + ru * RS + v;
+    const float* wb = ws + cg * NO;
+    switch (ph) {
+      case 0: stconv_phase<K, NO, TX, 0, 0>(xb, wb, acc); break;
+      case 1: stconv_phase<K, NO, TX, 0, 1>(xb, wb, acc); break;
+      case 2: stconv_phase<K, NO, TX, 1, 0>(xb, wb, acc); break;
+      default: stconv_phase<K, NO, TX, 1, 1>(xb, wb, acc); break;
+    }
+    __syncthreads();  // this buffer is refilled two stages on
+  }
+  const size_t oplane = (size_t)Ho * Wo;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const int Y = 2 * (U0 + i * RW + ru) + py, X = 2 * (V0 + v) + px;
+    if (Y >= Ho || X >= Wo) continue;
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      const int n = n0 + cg * NO + j;
+      if (n >= N) continue;
+      float* o = out + ((size_t)b * N + n) * oplane + (size_t)Y * Wo + X;
+      *o = accumulate ? *o + acc[i][j] : acc[i][j] + (bias ? bias[n] : 0.f);
+    }
+  }
+}
+
 // ------------------------------------------- dense stride-2 convs as GEMMs
 // The dense convolutions of the blocks (3x3 stride 2 in the encoder, 4x4
 // stride-2 transposed in the decoder, pad 1, one group) and their input
@@ -1170,9 +1407,40 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
 #undef STDA_IGEMM
   };
   auto dense_s2 = [](int k, int s, int p, int g, bool tr) { return g == 1 && s == 2 && p == 1 && k == (tr ? 4 : 3); };
+  // direct stride-2 conv (T: transposed) of src [B][M][Hs][Ws] into N channels
+  auto dconv = [&](bool T, int K, const float* src, const float* w, const float* bias, float* out, int M, int Hs,
+                   int Ws, int N, int accumulate) {
+    const int no = N >= 32 ? 16 : N >= 16 ? 8 : 4;
+    const int tx = (T ? Ws : Ws / 2) >= 32 ? 32 : 16;
+    int tiles;
+    if (T)
+      tiles = cdiv(Ws, tx) * cdiv(Hs, tx == 32 ? 2 : 4);
+    else
+      tiles = cdiv(Ws / 2, tx) * cdiv(Hs / 2, tx == 32 ? 8 : 16);
+    const dim3 grid(tiles, cdiv(N, 2 * no), B);
+    auto go = [&](auto kern, size_t smem) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<grid, 256, smem, st>>>(src, w, bias, out, M, Hs, Ws, N, accumulate);
+    };
+#define STDA_DC1(KERN, GEO, KS, NO, TX) go(KERN<KS, NO, TX>, GEO<KS, NO, TX>::smem())
+#define STDA_DC(KERN, GEO, KS)                                                                              \
+  (no == 16 ? (tx == 32 ? STDA_DC1(KERN, GEO, KS, 16, 32) : STDA_DC1(KERN, GEO, KS, 16, 16))                \
+            : no == 8 ? (tx == 32 ? STDA_DC1(KERN, GEO, KS, 8, 32) : STDA_DC1(KERN, GEO, KS, 8, 16))        \
+                      : (tx == 32 ? STDA_DC1(KERN, GEO, KS, 4, 32) : STDA_DC1(KERN, GEO, KS, 4, 16)))
+    if (T)
+      K == 4 ? STDA_DC(k_stconv, StconvGeo, 4) : STDA_DC(k_stconv, StconvGeo, 3);
+    else
+      K == 4 ? STDA_DC(k_sconv, SconvGeo, 4) : STDA_DC(k_sconv, SconvGeo, 3);
+#undef STDA_DC
+#undef STDA_DC1
+  };
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
     if (!run) return;
+    if (dense_s2(k, s, p, g, tr) && h % 2 == 0 && wd % 2 == 0) {
+      dconv(tr, k, x, w, bias, y, Ci, h, wd, Co, 0);
+      return;
+    }
     if (dense_s2(k, s, p, g, tr)) {
       igemm(tr ? DEC_FWD : ENC_FWD, x, w, bias, y, Ci, h, wd, Co, Ho, Wo);
       return;
@@ -1366,6 +1634,11 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
     if (!run) return;
+    if (dense_s2(k, s, p, g, tr) && hh % 2 == 0 && ww % 2 == 0) {
+      // encoder: transposed 3x3 of dy; decoder: 4x4 stride-2 conv of dy
+      dconv(!tr, k, dy, w, nullptr, dx, Co, Ho, Wo, Ci, 1);
+      return;
+    }
     if (dense_s2(k, s, p, g, tr)) {
       igemm(tr ? DEC_DGRAD : ENC_DGRAD, dy, w, nullptr, dx, Co, Ho, Wo, Ci, hh, ww);
       return;
