@@ -322,6 +322,46 @@ def run_serving(seconds=3.0, warm=1.0, streams=512, rate=20.0, flush_ms=0.25, se
             "serve_bytes": ctx.serve_bytes()}
 
 
+
+def train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda):
+    """The fwd+bwd training step on 64 windows of 3 x 256 x 128 (MSE against the
+    clean maps), BN with running statistics and in training mode."""
+    import torch
+
+    wt = workload("train_bf16_b64_3x256x128")
+    gt = wt.gen
+    tctx = stda.Context(gt.P, gt.Q, wt.batch, "bf16", 0)
+    tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, first_window(rank, wt.batch), wt.batch, dtype=torch.bfloat16)
+    for _ in range(2):
+        tctx.backward(tx, target=tclean)
+    def time_steps(step):
+        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.train_steps)]
+        barrier()
+        for i in range(args.train_steps):
+            flush.fill_(i & 0xFF)
+            tev[i][0].record(stream)
+            step()
+            tev[i][1].record(stream)
+        barrier()
+        tms = [a.elapsed_time(b) for a, b in tev]
+        return reduce_max(sum(tms), dist, dev), tms
+
+    ttot, tms = time_steps(lambda: tctx.backward(tx, target=tclean))
+    tctx.backward_bn(tx, target=tclean, mode="batch")
+    btot, _ = time_steps(lambda: tctx.backward_bn(tx, target=tclean, mode="batch"))
+    train = {"value": whole_job_rate(world, wt.batch, args.train_steps, ttot), "unit": UNIT,
+             "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
+             "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
+             "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
+             "l2": "flushed between timed steps",
+             "bn_batch_statistics": {"value": whole_job_rate(world, wt.batch, args.train_steps, btot),
+                                     "ms_per_step": btot / args.train_steps,
+                                     "step": "the same with BatchNorm in training mode (batch statistics)"}}
+    del tctx
+    return train
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +373,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the fwd+bwd training-step measurement")
     ap.add_argument("--train-steps", type=int, default=5)
+    ap.add_argument("--train-only", action="store_true", help="run only the training-step measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency measurement")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
@@ -361,6 +402,22 @@ def main():
 
     Bld.build()
     from paper_2307_09063_gb300 import stda
+
+    if args.train_only:
+        # the training leg alone (for launch lists of the training kernels)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+        def barrier():
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        train = train_leg(args, rank, world, dist, dev, torch.cuda.current_stream(), flush, barrier, stda)
+        if rank == 0:
+            print(json.dumps({"train_fwd_bwd": train}))
+        if dist:
+            dist.destroy_process_group()
+        return
 
     g = w.gen
     B, H, W = w.batch, g.P, g.Q
@@ -424,37 +481,7 @@ def main():
     # on 64 windows of 3 x 256 x 128, one step per timed iteration
     train = None
     if not args.no_train and world >= 1:
-        wt = workload("train_bf16_b64_3x256x128")
-        gt = wt.gen
-        tctx = stda.Context(gt.P, gt.Q, wt.batch, "bf16", 0)
-        tx, tclean, _, _ = stda.generate(gt, 0, wt.cid, first_window(rank, wt.batch), wt.batch, dtype=torch.bfloat16)
-        for _ in range(2):
-            tctx.backward(tx, target=tclean)
-        def time_steps(step):
-            tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.train_steps)]
-            barrier()
-            for i in range(args.train_steps):
-                flush.fill_(i & 0xFF)
-                tev[i][0].record(stream)
-                step()
-                tev[i][1].record(stream)
-            barrier()
-            tms = [a.elapsed_time(b) for a, b in tev]
-            return reduce_max(sum(tms), dist, dev), tms
-
-        ttot, tms = time_steps(lambda: tctx.backward(tx, target=tclean))
-        tctx.backward_bn(tx, target=tclean, mode="batch")
-        btot, _ = time_steps(lambda: tctx.backward_bn(tx, target=tclean, mode="batch"))
-        train = {"value": whole_job_rate(world, wt.batch, args.train_steps, ttot), "unit": UNIT,
-                 "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
-                 "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
-                 "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
-                 "l2": "flushed between timed steps",
-                 "bn_batch_statistics": {"value": whole_job_rate(world, wt.batch, args.train_steps, btot),
-                                         "ms_per_step": btot / args.train_steps,
-                                         "step": "the same with BatchNorm in training mode (batch statistics)"}}
-        del tctx
+        train = train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda)
 
     hbm_gbs, bf16_tf, bf16_tf_sus, peak_src = load_peaks()
     bytes_per_step = B * 4 * H * W * esz  # 3 input maps + 1 output map per window
