@@ -169,13 +169,30 @@ stda_status stda_set_buffers(stda_ctx* ctx, const float* host_src, size_t n);
 stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
                          int H, int W, struct CUstream_st* stream);
 
+/* The same forward pass on host buffers, end to end: h_in [B][frames][H][W]
+ * and h_out [B][1][H][W] in host memory, element type as for stda_forward
+ * (page-locked memory lets the copies overlap kernels; pageable memory works
+ * but its copies do not overlap). The input is copied to one of two device
+ * staging buffers on an internal stream that waits only for the forward that
+ * last read that buffer (two calls back), so a call's input copy overlaps the
+ * previous call's kernels; the forward runs on `stream` once its input has
+ * landed, and the output is copied back on a second internal stream, which
+ * `stream` then waits for. So: h_in must hold its final contents when the
+ * call is made (it is not ordered after work already queued on `stream`);
+ * h_out is complete once `stream` has been synchronised; work queued on
+ * `stream` after the call follows the copy back. Calls on one context must
+ * use one stream. The first call allocates the staging buffers (two pairs of
+ * max_batch windows of the context's H x W). Shapes as for stda_forward. */
+stda_status stda_forward_host(stda_ctx* ctx, const void* h_in, void* h_out, int B,
+                              int H, int W, struct CUstream_st* stream);
+
 /* Training step (adjoint of the forward pass): runs the network's forward
  * pass with a tape and its exact adjoint, in FP32 on the CUDA cores, with
  * batch normalisation in inference form (frozen running statistics;
  * gamma and beta receive gradients; stda_backward_bn below selects training
  * mode). Weight and BN gradients are reduced
- * per chunk of four windows in FP32 and across chunks in FP64; the loss is
- * an FP64 sum.
+ * in FP32 over slices of the batch's pixels and across slices in FP64 (in a
+ * fixed order); the loss is an FP64 sum.
  *   d_in      [B][3][H][W] in the context's element type
  *   d_target  [B][1][H][W] clean maps in the context's element type; the
  *             loss is their mean squared error (Sec. V-C trains the
@@ -208,8 +225,8 @@ typedef enum {
  * the BN buffers (per BN: mean[C] then var[C]; stem, then per block BN1,
  * BN2, BN3, BN), from which a caller updates the running statistics (e.g.
  * running = (1 - m) running + m batch). The statistics are two-pass
- * (mean, then mean squared deviation), FP32 per chunk of four windows and
- * FP64 across chunks. STDA_ERR_INVALID_ARG on an unknown mode. */
+ * (mean, then mean squared deviation), FP32 over slices of the batch's
+ * pixels and FP64 across slices. STDA_ERR_INVALID_ARG on an unknown mode. */
 stda_status stda_backward_bn(stda_ctx* ctx, const void* d_in, const void* d_target,
                              const float* d_gout, float* d_gparams, double* d_loss,
                              float* d_gin, float* d_out, int B, int H, int W,

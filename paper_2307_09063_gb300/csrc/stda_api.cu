@@ -417,6 +417,14 @@ struct stda_ctx {
   size_t scratch_size = 0;
   int* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
+  // host-buffer forward: two staging pairs (max_batch windows each), copy
+  // streams, and per pair the events input copied / forward done / output copied
+  void* d_hin[2] = {};
+  void* d_hout[2] = {};
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_h[2] = {}, ev_f[2] = {}, ev_d[2] = {};
+  bool f_recorded[2] = {};
+  uint64_t host_calls = 0;
   std::string err;
 };
 
@@ -547,6 +555,15 @@ stda_status stda_destroy(stda_ctx* c) {
   if (c->d_train) cudaFree(c->d_train);
   if (c->d_target32) cudaFree(c->d_target32);
   if (c->serve) stda::serve_delete(c->serve);
+  for (int k = 0; k < 2; ++k) {
+    if (c->d_hin[k]) cudaFree(c->d_hin[k]);
+    if (c->d_hout[k]) cudaFree(c->d_hout[k]);
+    if (c->ev_h[k]) cudaEventDestroy(c->ev_h[k]);
+    if (c->ev_f[k]) cudaEventDestroy(c->ev_f[k]);
+    if (c->ev_d[k]) cudaEventDestroy(c->ev_d[k]);
+  }
+  if (c->h2d) cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
   delete c;
   return STDA_OK;
 }
@@ -642,6 +659,47 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
       return fail(c, STDA_ERR_UNSUPPORTED, "forward: unknown precision");
   }
   if (e) return cuda_fail(c, e, "forward");
+  return STDA_OK;
+}
+
+stda_status stda_forward_host(stda_ctx* c, const void* h_in, void* h_out, int B, int H, int W, cudaStream_t st) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  if (B < 0 || B > c->cfg.max_batch) return fail(c, STDA_ERR_SHAPE, "forward_host: batch out of range");
+  if (!shape_ok(H, W)) return fail(c, STDA_ERR_SHAPE, "forward_host: H and W must be positive multiples of 8");
+  if ((size_t)B * H * W > (size_t)c->cfg.max_batch * c->cfg.H * c->cfg.W)
+    return fail(c, STDA_ERR_SHAPE, "forward_host: B*H*W exceeds the context");
+  if (B == 0) return STDA_OK;
+  if (!h_in || !h_out) return fail(c, STDA_ERR_INVALID_ARG, "forward_host: null pointer");
+  const size_t es = elem_size(c->cfg.prec);
+  const size_t cap = (size_t)c->cfg.max_batch * c->cfg.H * c->cfg.W * es;
+  cudaError_t e = cudaSuccess;
+  if (!c->h2d) {
+    for (int k = 0; k < 2 && !e; ++k)
+      if (!(e = cudaMalloc(&c->d_hin[k], cap * c->frames))) e = cudaMalloc(&c->d_hout[k], cap);
+    if (!e) e = cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && !e; ++k)
+      if (!(e = cudaEventCreateWithFlags(&c->ev_h[k], cudaEventDisableTiming)) &&
+          !(e = cudaEventCreateWithFlags(&c->ev_f[k], cudaEventDisableTiming)))
+        e = cudaEventCreateWithFlags(&c->ev_d[k], cudaEventDisableTiming);
+    if (e) return cuda_fail(c, e, "forward_host: staging");
+  }
+  // staging pair k alternates between calls: this call's input copy only
+  // waits for the forward that last read pair k (two calls back)
+  const int k = (int)(c->host_calls++ & 1);
+  const size_t nin = (size_t)B * c->frames * H * W * es, nout = (size_t)B * H * W * es;
+  if (c->f_recorded[k] && (e = cudaStreamWaitEvent(c->h2d, c->ev_f[k], 0))) return cuda_fail(c, e, "forward_host");
+  if ((e = cudaMemcpyAsync(c->d_hin[k], h_in, nin, cudaMemcpyHostToDevice, c->h2d)) ||
+      (e = cudaEventRecord(c->ev_h[k], c->h2d)) || (e = cudaStreamWaitEvent(st, c->ev_h[k], 0)))
+    return cuda_fail(c, e, "forward_host: input copy");
+  const stda_status r = stda_forward(c, c->d_hin[k], c->d_hout[k], B, H, W, st);
+  if (r != STDA_OK) return r;
+  if ((e = cudaEventRecord(c->ev_f[k], st))) return cuda_fail(c, e, "forward_host");
+  c->f_recorded[k] = true;
+  if ((e = cudaStreamWaitEvent(c->d2h, c->ev_f[k], 0)) ||
+      (e = cudaMemcpyAsync(h_out, c->d_hout[k], nout, cudaMemcpyDeviceToHost, c->d2h)) ||
+      (e = cudaEventRecord(c->ev_d[k], c->d2h)) || (e = cudaStreamWaitEvent(st, c->ev_d[k], 0)))
+    return cuda_fail(c, e, "forward_host: output copy");
   return STDA_OK;
 }
 

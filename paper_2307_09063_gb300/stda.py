@@ -67,6 +67,7 @@ def lib():
         L.stda_num_params_frames.argtypes = [ctypes.c_int]
         L.stda_init_params_frames.argtypes = [ctypes.c_uint64, ctypes.c_int, _VP, _VP]
         L.stda_forward.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
+        L.stda_forward_host.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_device_status.argtypes = [_VP]
         L.stda_last_error.restype = ctypes.c_char_p
         L.stda_last_error.argtypes = [_VP]
@@ -230,6 +231,22 @@ class Context:
         if out is None:
             out = torch.empty((B, 1, H, W), dtype=x.dtype, device=x.device)
         self._check(self.forward_raw(x, out, B, H, W, stream))
+        return out
+
+    def forward_host(self, x, out=None, stream=None):
+        """stda_forward_host: x a CPU tensor [B][frames][H][W] (pinned for
+        overlapped copies) whose contents are final, out a CPU tensor
+        [B][1][H][W] (allocated pinned if None), complete once `stream` (the
+        current stream if None) is synchronised."""
+        import torch
+
+        assert not x.is_cuda and x.is_contiguous() and x.dtype == self.io_dtype and x.dim() == 4
+        assert x.shape[1] == self.frames
+        B, _, H, W = x.shape
+        if out is None:
+            out = torch.empty((B, 1, H, W), dtype=x.dtype).pin_memory()
+        assert not out.is_cuda and out.is_contiguous() and out.dtype == x.dtype and out.numel() == B * H * W
+        self._check(lib().stda_forward_host(self.h, _ptr(x), _ptr(out), B, H, W, _stream(stream)))
         return out
 
     def backward(self, x, target=None, gout=None, want_gin=False, want_out=False, stream=None):
