@@ -852,6 +852,137 @@ __global__ void __launch_bounds__(256, 3) k_wgemm(WgArgs a) {
   }
 }
 
+// k_wgemm with the block shape fixed at compile time (the six dense convs of
+// the network): MP rows, BN columns per block, KG k-groups of
+// P = (MP / 4) (BN / 4) threads, 256 threads (8 warps) in all. Every stage
+// index, swizzle and loop bound is then a constant: each lane fills MP / 8
+// rows and BN / 8 columns of a 32-pixel stage.
+template <int KS, int MP, int BN, int KG>
+__global__ void __launch_bounds__(256, 2) k_wgemm_t(WgArgs a) {
+  constexpr int KK = KS * KS, P = (MP / 4) * (BN / 4), RA = MP / 8, RG = BN / 8;
+  static_assert(P * KG <= 256 && MP % 8 == 0 && BN % 8 == 0, "block shape");
+  constexpr int NGRP = (8 + KG - 1) / KG;  // 4-pixel groups per k-group and stage
+  __shared__ __align__(16) float As[MP * 32];
+  __shared__ __align__(16) float Gs[BN * 32];
+  __shared__ int tab[BN];
+  __shared__ __align__(16) float red[KG > 1 ? KG * 16 * P : 1];
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
+  const int kg = tid / P, pos = tid % P, tm = pos / (BN / 4), tn = pos % (BN / 4);
+  const bool act = kg < KG;
+  const int n0 = blockIdx.y * BN;
+  const int np = a.Hp * a.Wp;
+  const int K = a.B * np, k0 = blockIdx.x * a.S, k1 = min(K, k0 + a.S);
+  const int gplane = a.Hg * a.Wg;
+  for (int c = tid; c < BN; c += 256) {
+    const int col = n0 + c, ch = col / KK, t = col % KK, ky = t / KS, kx = t % KS;
+    tab[c] = col < a.N ? ((ch * gplane + ky * a.Wg + kx) << 4) | (ky << 2) | kx : -1;
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float ra[RA], rg[RG];
+  const size_t rstride = (size_t)8 * np;  // rows wq, wq + 8, ...
+  auto fetch = [&](int s0) {
+    const int m = s0 + lane;
+    const bool mok = m < k1;
+    int b = 0, q = 0, Y = 0, X = 0;
+    if (mok) {
+      b = (unsigned)m / (unsigned)np;
+      q = m - b * np;
+      Y = (unsigned)q / (unsigned)a.Wp;
+      X = q - Y * a.Wp;
+    }
+    const float* ab = a.a + ((size_t)b * a.M + wq) * np + q;
+#pragma unroll
+    for (int i = 0; i < RA; ++i) ra[i] = mok && wq + 8 * i < a.M ? ab[i * rstride] : 0.f;
+    const int gy0 = a.s * Y - a.p, gx0 = a.s * X - a.p;
+    const float* gb = a.g + (size_t)b * a.CG * gplane + (gy0 * a.Wg + gx0);
+#pragma unroll
+    for (int j = 0; j < RG; ++j) {
+      const int e = tab[wq + 8 * j];
+      rg[j] = mok && e >= 0 && (unsigned)(gy0 + ((e >> 2) & 3)) < (unsigned)a.Hg &&
+                      (unsigned)(gx0 + (e & 3)) < (unsigned)a.Wg
+                  ? gb[e >> 4]
+                  : 0.f;
+    }
+  };
+  __syncthreads();  // the column table
+  if (k0 < k1) fetch(k0);
+  // this lane's stage slots: row wq + 8 i sits in 16-byte group (lane / 4) ^ ((row / 4) mod 8)
+  const int so = lane & 3, sg = lane >> 2;
+  const int xa = tm & 7, xg = tn & 7;
+  for (int s0 = k0; s0 < k1; s0 += 32) {
+    __syncthreads();  // the previous stage's reads are done
+#pragma unroll
+    for (int i = 0; i < RA; ++i) {
+      const int r = wq + 8 * i;
+      As[r * 32 + ((sg ^ ((r >> 2) & 7)) << 2) + so] = ra[i];
+    }
+#pragma unroll
+    for (int j = 0; j < RG; ++j) {
+      const int c = wq + 8 * j;
+      Gs[c * 32 + ((sg ^ ((c >> 2) & 7)) << 2) + so] = rg[j];
+    }
+    __syncthreads();
+    if (s0 + 32 < k1) fetch(s0 + 32);
+    if (act) {
+#pragma unroll
+      for (int g2 = 0; g2 < NGRP; ++g2) {
+        const int grp = kg + g2 * KG;
+        if (grp >= 8) break;
+        const float* ap = As + tm * 128 + ((grp ^ xa) << 2);
+        const float* gp = Gs + tn * 128 + ((grp ^ xg) << 2);
+        float4 av[4], gv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = *(const float4*)(ap + 32 * i);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gv[j] = *(const float4*)(gp + 32 * j);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] += av[i].x * gv[j].x;
+            acc[i][j] += av[i].y * gv[j].y;
+            acc[i][j] += av[i].z * gv[j].z;
+            acc[i][j] += av[i].w * gv[j].w;
+          }
+      }
+    }
+  }
+  if (KG > 1) {
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(kg * 16 + i * 4 + j) * P + pos] = acc[i][j];
+    }
+    __syncthreads();
+    if (kg == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float r = red[(i * 4 + j) * P + pos];
+#pragma unroll
+          for (int k = 1; k < KG; ++k) r += red[(k * 16 + i * 4 + j) * P + pos];
+          acc[i][j] = r;
+        }
+    }
+  }
+  if (kg == 0) {
+    float* out = a.part + (size_t)blockIdx.x * a.M * a.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int row = tm * 4 + i, col = n0 + tn * 4 + j;
+        if (row < a.M && col < a.N) out[(size_t)row * a.N + col] = acc[i][j];
+      }
+  }
+}
+
 __device__ float block_sum(float v, float* sh) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1593,8 +1724,28 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       const int P = (wa.MP / 4) * (wa.BN / 4);
       wa.KG = std::min(8, 256 / P);
       const int threads = cdiv((long)P * wa.KG, 32) * 32, nw = threads / 32;
-      if (wa.MP <= kWgRows * nw && wa.BN <= kWgCols * nw && (long)B * wa.Hp * wa.Wp < (1L << 30) &&
-          (long)wa.CG * wa.Hg * wa.Wg < (1L << 27)) {
+      // the network's six shapes: fixed-shape kernels (MP, BN, KG)
+      const bool fits = (long)B * wa.Hp * wa.Wp < (1L << 30) && (long)wa.CG * wa.Hg * wa.Wg < (1L << 27);
+      auto fixed = [&](auto kern, int bn) {
+        const int ntf = cdiv(wa.N, bn);
+        const Slices sl = slices((long)B * wa.Hp * wa.Wp, ntf, (long)wa.M * wa.N, 32, 2, 256);
+        wa.S = sl.S;
+        kern<<<dim3(sl.n, ntf), 256, 0, st>>>(wa);
+        reduce(part, sl.n, wa.M * wa.N, 1, 0, dst);
+      };
+      if (fits && wa.MP == wa.M) {
+        const int key = k * 10000 + wa.M * 1000 + wa.N;
+        switch (key) {
+          case 3 * 10000 + 16 * 1000 + 72: fixed(k_wgemm_t<3, 16, 72, 3>, 72); return;
+          case 3 * 10000 + 32 * 1000 + 144: fixed(k_wgemm_t<3, 32, 48, 2>, 48); return;
+          case 3 * 10000 + 64 * 1000 + 288: fixed(k_wgemm_t<3, 64, 32, 2>, 32); return;
+          case 4 * 10000 + 64 * 1000 + 512: fixed(k_wgemm_t<4, 64, 64, 1>, 64); return;
+          case 4 * 10000 + 32 * 1000 + 256: fixed(k_wgemm_t<4, 32, 128, 1>, 128); return;
+          case 4 * 10000 + 16 * 1000 + 128: fixed(k_wgemm_t<4, 16, 128, 2>, 128); return;
+          default: break;
+        }
+      }
+      if (wa.MP <= kWgRows * nw && wa.BN <= kWgCols * nw && fits) {
         const Slices sl = slices((long)B * wa.Hp * wa.Wp, nt, (long)wa.M * wa.N, 32, 4, 256);
         wa.S = sl.S;
         const size_t smem = std::max(sizeof(float) * (32 * (wa.MP + wa.BN) + wa.BN),
