@@ -365,20 +365,20 @@ __device__ __forceinline__ void load_w(const float* p, float (&wv)[NO]) {
   }
 }
 
-template <int K, int NO, int TX>
+template <int K, int NO, int TX, int NPP>
 struct SconvGeo {
-  static constexpr int KK = K * K, RW = 32 / TX, NP = 2, TY = 4 * NP * RW, R = 2 * TY + K - 2;
+  static constexpr int NP = NPP, KK = K * K, RW = 32 / TX, TY = 4 * NP * RW, R = 2 * TY + K - 2;
   static constexpr int PW = TX == 32 ? 33 : 20;  // parity-plane row (TX + 1, padded against conflicts)
   static constexpr int RS = 2 * PW, CS = R * RS, NB = 2 * NO;
   static constexpr int NX = kDcMC * CS, NW = kDcMC * KK * NB, STAGE = NX + NW;
   static constexpr size_t smem() { return sizeof(float) * 2 * STAGE; }
 };
 
-template <int K, int NO, int TX>
+template <int K, int NO, int TX, int NP_>
 __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, const float* __restrict__ w,
                                                const float* __restrict__ bias, float* __restrict__ out, int M,
                                                int Hs, int Ws, int N, int accumulate) {
-  using G = SconvGeo<K, NO, TX>;
+  using G = SconvGeo<K, NO, TX, NP_>;
   constexpr int KK = G::KK, RW = G::RW, NP = G::NP, TY = G::TY, R = G::R, PW = G::PW, RS = G::RS, CS = G::CS;
   constexpr int NB = G::NB;
   extern __shared__ __align__(16) float dsm[];
@@ -457,9 +457,9 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
   }
 }
 
-template <int K, int NO, int TX>
+template <int K, int NO, int TX, int NPP>
 struct StconvGeo {
-  static constexpr int KK = K * K, RW = 32 / TX, NP = 2, TU = NP * RW, R = TU + 2;
+  static constexpr int NP = NPP, KK = K * K, RW = 32 / TX, TU = NP * RW, R = TU + 2;
   static constexpr int RS = TX == 32 ? 34 : 48;  // source tile row (TX + 2, padded against conflicts)
   static constexpr int CS = R * RS, NB = 2 * NO;
   static constexpr int NX = kDcMC * CS, NW = kDcMC * KK * NB, STAGE = NX + NW;
@@ -468,9 +468,9 @@ struct StconvGeo {
 
 // the taps of output phase (PY, PX) of k_stconv: ky = ky0 + 2 sy < K with
 // ky0 = (PY + 1) mod 2, source row offset (PY + 1 - ky) / 2 (likewise x)
-template <int K, int NO, int TX, int PY, int PX>
-__device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, float (&acc)[2][NO]) {
-  using G = StconvGeo<K, NO, TX>;
+template <int K, int NO, int TX, int NP, int PY, int PX>
+__device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, float (&acc)[NP][NO]) {
+  using G = StconvGeo<K, NO, TX, NP>;
   constexpr int KY0 = (PY + 1) & 1, KX0 = (PX + 1) & 1;
   constexpr int NTY = KY0 + 2 < K ? 2 : 1, NTX = KX0 + 2 < K ? 2 : 1;
 #pragma unroll
@@ -492,11 +492,11 @@ __device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, f
       }
 }
 
-template <int K, int NO, int TX>
+template <int K, int NO, int TX, int NP_>
 __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, const float* __restrict__ w,
                                                 const float* __restrict__ bias, float* __restrict__ out, int M,
                                                 int Hs, int Ws, int N, int accumulate) {
-  using G = StconvGeo<K, NO, TX>;
+  using G = StconvGeo<K, NO, TX, NP_>;
   constexpr int KK = G::KK, RW = G::RW, NP = G::NP, TU = G::TU, R = G::R, RS = G::RS, NB = G::NB;
   extern __shared__ __align__(16) float dsm[];
   const int Ho = 2 * Hs, Wo = 2 * Ws;
@@ -542,10 +542,10 @@ __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, c
     const float* xb = xs + ru * RS + v;
     const float* wb = ws + cg * NO;
     switch (ph) {
-      case 0: stconv_phase<K, NO, TX, 0, 0>(xb, wb, acc); break;
-      case 1: stconv_phase<K, NO, TX, 0, 1>(xb, wb, acc); break;
-      case 2: stconv_phase<K, NO, TX, 1, 0>(xb, wb, acc); break;
-      default: stconv_phase<K, NO, TX, 1, 1>(xb, wb, acc); break;
+      case 0: stconv_phase<K, NO, TX, NP, 0, 0>(xb, wb, acc); break;
+      case 1: stconv_phase<K, NO, TX, NP, 0, 1>(xb, wb, acc); break;
+      case 2: stconv_phase<K, NO, TX, NP, 1, 0>(xb, wb, acc); break;
+      default: stconv_phase<K, NO, TX, NP, 1, 1>(xb, wb, acc); break;
     }
     __syncthreads();  // this buffer is refilled two stages on
   }
@@ -1543,27 +1543,32 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
                    int Ws, int N, int accumulate) {
     const int no = N >= 32 ? 16 : N >= 16 ? 8 : 4;
     const int tx = (T ? Ws : Ws / 2) >= 32 ? 32 : 16;
-    int tiles;
-    if (T)
-      tiles = cdiv(Ws, tx) * cdiv(Hs, tx == 32 ? 2 : 4);
-    else
-      tiles = cdiv(Ws / 2, tx) * cdiv(Hs / 2, tx == 32 ? 8 : 16);
-    const dim3 grid(tiles, cdiv(N, 2 * no), B);
+    // pixels per thread: 2 with 16 channels; with 4 or 8 channels 4 (the
+    // weights feed more FMAs) where that still gives about six blocks per SM
+    auto tiles_for = [&](int np) {
+      const int rw = 32 / tx;
+      return T ? cdiv(Ws, tx) * cdiv(Hs, np * rw) : cdiv(Ws / 2, tx) * cdiv(Hs / 2, 4 * np * rw);
+    };
+    const long want = (long)device_sms() * 6;
+    const int np = no < 16 && (long)tiles_for(4) * cdiv(N, 2 * no) * B >= want ? 4 : 2;
+    const dim3 grid(tiles_for(np), cdiv(N, 2 * no), B);
     auto go = [&](auto kern, size_t smem) {
       if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<grid, 256, smem, st>>>(src, w, bias, out, M, Hs, Ws, N, accumulate);
     };
-#define STDA_DC1(KERN, GEO, KS, NO, TX) go(KERN<KS, NO, TX>, GEO<KS, NO, TX>::smem())
+#define STDA_DC2(KERN, GEO, KS, NO, TX)                                                            \
+  (NO < 16 && np == 4 ? go(KERN<KS, NO, TX, (NO < 16 ? 4 : 2)>, GEO<KS, NO, TX, (NO < 16 ? 4 : 2)>::smem()) \
+                      : go(KERN<KS, NO, TX, 2>, GEO<KS, NO, TX, 2>::smem()))
 #define STDA_DC(KERN, GEO, KS)                                                                              \
-  (no == 16 ? (tx == 32 ? STDA_DC1(KERN, GEO, KS, 16, 32) : STDA_DC1(KERN, GEO, KS, 16, 16))                \
-            : no == 8 ? (tx == 32 ? STDA_DC1(KERN, GEO, KS, 8, 32) : STDA_DC1(KERN, GEO, KS, 8, 16))        \
-                      : (tx == 32 ? STDA_DC1(KERN, GEO, KS, 4, 32) : STDA_DC1(KERN, GEO, KS, 4, 16)))
+  (no == 16 ? (tx == 32 ? STDA_DC2(KERN, GEO, KS, 16, 32) : STDA_DC2(KERN, GEO, KS, 16, 16))                \
+            : no == 8 ? (tx == 32 ? STDA_DC2(KERN, GEO, KS, 8, 32) : STDA_DC2(KERN, GEO, KS, 8, 16))        \
+                      : (tx == 32 ? STDA_DC2(KERN, GEO, KS, 4, 32) : STDA_DC2(KERN, GEO, KS, 4, 16)))
     if (T)
       K == 4 ? STDA_DC(k_stconv, StconvGeo, 4) : STDA_DC(k_stconv, StconvGeo, 3);
     else
       K == 4 ? STDA_DC(k_sconv, SconvGeo, 4) : STDA_DC(k_sconv, SconvGeo, 3);
 #undef STDA_DC
-#undef STDA_DC1
+#undef STDA_DC2
   };
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
