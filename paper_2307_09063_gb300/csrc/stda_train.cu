@@ -22,7 +22,6 @@ namespace {
 constexpr int kT = 256;
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
-inline dim3 grid1(long n) { return dim3(cdiv(n, kT)); }
 // grid of the per-plane elementwise kernels: x over the n pixels of a plane,
 // y over the planes (each block loops over planes y, y + gridDim.y, ...)
 inline dim3 gridp(long total, long n) { return dim3(cdiv(n, kT), (unsigned)std::min(total / n, 65535L)); }
@@ -234,6 +233,54 @@ __global__ void __launch_bounds__(256) k_dw(const float* __restrict__ src, const
   }
   float* dp = dst + plane + q;
   *dp = accumulate ? *dp + acc : acc;
+}
+
+// k_dw with four horizontally adjacent outputs per thread (W a multiple of
+// 4): each source row is read as one 16-byte load plus the two neighbours.
+template <int K, bool FLIP>
+__global__ void __launch_bounds__(256) k_dw4(const float* __restrict__ src, const float* __restrict__ w,
+                                             const float* __restrict__ bias, float* __restrict__ dst, int C, int H,
+                                             int W, int accumulate) {
+  constexpr int P = (K - 1) / 2;
+  const int W4 = W >> 2, q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H * W4) return;
+  const int c = blockIdx.y, Y = q / W4, X0 = (q - Y * W4) * 4;
+  const size_t plane = ((size_t)blockIdx.z * C + c) * H * W;
+  const float* sp = src + plane;
+  float wk[K * K];
+#pragma unroll
+  for (int t = 0; t < K * K; ++t) wk[t] = w[c * K * K + t];
+  const float b0 = bias ? bias[c] : 0.f;
+  float acc[4] = {b0, b0, b0, b0};
+#pragma unroll
+  for (int ky = 0; ky < K; ++ky) {
+    const int sy = FLIP ? Y + P - ky : Y - P + ky;
+    if ((unsigned)sy >= (unsigned)H) continue;
+    const float* row = sp + (size_t)sy * W + X0;
+    float v[4 + 2 * P];  // columns X0 - P .. X0 + 3 + P
+    const float4 m = *(const float4*)row;
+    v[P] = m.x;
+    v[P + 1] = m.y;
+    v[P + 2] = m.z;
+    v[P + 3] = m.w;
+    if (P) {
+      v[0] = X0 > 0 ? row[-1] : 0.f;
+      v[4 + 2 * P - 1] = X0 + 4 < W ? row[4] : 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int kx = 0; kx < K; ++kx) acc[o] += v[o + (FLIP ? K - 1 - kx : kx)] * wk[ky * K + kx];
+  }
+  float* dp = dst + plane + (size_t)Y * W + X0;
+  if (accumulate) {
+    const float4 o = *(const float4*)dp;
+    acc[0] += o.x;
+    acc[1] += o.y;
+    acc[2] += o.z;
+    acc[3] += o.w;
+  }
+  *(float4*)dp = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
 // Weight gradients of the stride-1, pad (K - 1) / 2 convs: the per-channel
@@ -1167,17 +1214,50 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, 
   if (j < n) out[j] = (float)a[j];
 }
 
+// The elementwise kernels take V = 4 consecutive elements per thread
+// (16-byte loads and stores; the plane size is then a multiple of 4) or V = 1.
+template <int V>
+__device__ __forceinline__ void ldv(const float* p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 f = *(const float4*)p;
+    v[0] = f.x;
+    v[1] = f.y;
+    v[2] = f.z;
+    v[3] = f.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = p[e];
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float (&v)[V]) {
+  if constexpr (V == 4) {
+    *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) p[e] = v[e];
+  }
+}
+
 // y = relu?(gam (x - mean) / sqrt(var + eps) + bet) per channel
+template <int V>
 __global__ void k_bn(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ gam,
                      const float* __restrict__ bet, const float* __restrict__ mean, const float* __restrict__ var,
                      int planes, int C, int n, int relu) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    const float v = gam[c] * (x[idx] - mean[c]) * rsqrtf(var[c] + 1e-5f) + bet[c];
-    y[idx] = relu ? fmaxf(v, 0.f) : v;
+    const float g = gam[c] * rsqrtf(var[c] + 1e-5f), m = mean[c], b = bet[c];
+    float v[V];
+    ldv<V>(x + idx, v);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const float o = g * (v[e] - m) + b;
+      v[e] = relu ? fmaxf(o, 0.f) : o;
+    }
+    stv<V>(y + idx, v);
   }
 }
 
@@ -1188,24 +1268,37 @@ struct BnP {
 __device__ __forceinline__ float bnv(const BnP& q, int c, float x) {
   return q.g[c] * (x - q.m[c]) * rsqrtf(q.v[c] + 1e-5f) + q.b[c];
 }
+template <int V>
 __global__ void k_stage1(const float* t1, const float* t2, const float* x, float* x1, BnP b1, BnP b2, BnP b3,
                          int planes, int C, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    x1[idx] = fmaxf(bnv(b1, c, t1[idx]) + bnv(b2, c, t2[idx]) + bnv(b3, c, x[idx]), 0.f);
+    float a1[V], a2[V], a3[V];
+    ldv<V>(t1 + idx, a1);
+    ldv<V>(t2 + idx, a2);
+    ldv<V>(x + idx, a3);
+#pragma unroll
+    for (int e = 0; e < V; ++e) a1[e] = fmaxf(bnv(b1, c, a1[e]) + bnv(b2, c, a2[e]) + bnv(b3, c, a3[e]), 0.f);
+    stv<V>(x1 + idx, a1);
   }
 }
 // y = ReLU(BN(u)) + r
+template <int V>
 __global__ void k_stage2(const float* u, const float* r, float* y, BnP bn, int planes, int C, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    y[idx] = fmaxf(bnv(bn, c, u[idx]), 0.f) + r[idx];
+    float a[V], b[V];
+    ldv<V>(u + idx, a);
+    ldv<V>(r + idx, b);
+#pragma unroll
+    for (int e = 0; e < V; ++e) a[e] = fmaxf(bnv(bn, c, a[e]), 0.f) + b[e];
+    stv<V>(y + idx, a);
   }
 }
 
@@ -1230,13 +1323,19 @@ __global__ void k_eca_s(const float* g, const float* k3, float* sc, int B, int C
   sc[idx] = 1.f / (1.f + expf(-z));
 }
 // out = s * y (+ skip)
+template <int V>
 __global__ void k_scale(const float* y, const float* sc, const float* skip, float* out, int planes, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const size_t idx = (size_t)pl * n + q;
-    const float v = sc[pl] * y[idx];
-    out[idx] = skip ? v + skip[idx] : v;
+    const float s = sc[pl];
+    float a[V], b[V];
+    ldv<V>(y + idx, a);
+    if (skip) ldv<V>(skip + idx, b);
+#pragma unroll
+    for (int e = 0; e < V; ++e) a[e] = skip ? s * a[e] + b[e] : s * a[e];
+    stv<V>(out + idx, a);
   }
 }
 
@@ -1317,33 +1416,51 @@ __global__ void k_eca_back(const float* ds, const float* sc, const float* g, con
   for (int j = 0; j < 3; ++j) dk_part[b * 3 + j] = dk[j];
 }
 // dy = s * dout + dg (the mean's adjoint, already divided by n)
+template <int V>
 __global__ void k_eca_dy(const float* dout, const float* sc, const float* dgm, float* dy, int planes, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const size_t idx = (size_t)pl * n + q;
-    dy[idx] = sc[pl] * dout[idx] + dgm[pl];
+    const float s = sc[pl], d = dgm[pl];
+    float a[V];
+    ldv<V>(dout + idx, a);
+#pragma unroll
+    for (int e = 0; e < V; ++e) a[e] = s * a[e] + d;
+    stv<V>(dy + idx, a);
   }
 }
 // dbn = dy [BN(u) > 0]
+template <int V>
 __global__ void k_relu_bn_mask(const float* dy, const float* u, BnP bn, float* dbn, int planes, int C, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    dbn[idx] = bnv(bn, c, u[idx]) > 0.f ? dy[idx] : 0.f;
+    float a[V], b[V];
+    ldv<V>(dy + idx, a);
+    ldv<V>(u + idx, b);
+#pragma unroll
+    for (int e = 0; e < V; ++e) a[e] = bnv(bn, c, b[e]) > 0.f ? a[e] : 0.f;
+    stv<V>(dbn + idx, a);
   }
 }
 // out (+)= a * gam / sqrt(var + eps)
+template <int V>
 __global__ void k_bn_dx(const float* a, BnP bn, float* out, int planes, int C, int n, int accumulate) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    const float v = a[idx] * bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
-    out[idx] = accumulate ? out[idx] + v : v;
+    const float g = bn.g[c] * rsqrtf(bn.v[c] + 1e-5f);
+    float v[V], o[V];
+    ldv<V>(a + idx, v);
+    if (accumulate) ldv<V>(out + idx, o);
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = accumulate ? o[e] + v[e] * g : v[e] * g;
+    stv<V>(out + idx, v);
   }
 }
 // Batch statistics of a BN input x[B][C][n]: part[chunk][c] = sum over the
@@ -1369,32 +1486,62 @@ __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__
 }
 // Batch-statistics BN adjoint: out (+)= gam / sigma (dy - (sum dy + xhat sum
 // dy xhat) / N), the two sums of this BN being gacc[dbet + c], gacc[dgam + c].
+template <int V>
 __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const double* __restrict__ gacc, long dgam,
                               long dbet, double N, float* out, int planes, int C, int n, int accumulate) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
-    const float is = rsqrtf(bn.v[c] + 1e-5f), xh = (x[idx] - bn.m[c]) * is;
-    const float corr = (float)((gacc[dbet + c] + (double)xh * gacc[dgam + c]) / N);
-    const float v = bn.g[c] * is * (dy[idx] - corr);
-    out[idx] = accumulate ? out[idx] + v : v;
+    const float is = rsqrtf(bn.v[c] + 1e-5f), m = bn.m[c], g = bn.g[c] * is;
+    const double sb = gacc[dbet + c], sg = gacc[dgam + c];
+    float d[V], xv[V], o[V];
+    ldv<V>(dy + idx, d);
+    ldv<V>(x + idx, xv);
+    if (accumulate) ldv<V>(out + idx, o);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const float xh = (xv[e] - m) * is;
+      const float corr = (float)((sb + (double)xh * sg) / N);
+      const float v = g * (d[e] - corr);
+      d[e] = accumulate ? o[e] + v : v;
+    }
+    stv<V>(out + idx, d);
   }
 }
 // dv = dx1 [x1 > 0]
+template <int V>
 __global__ void k_relu_mask(const float* d, const float* act, float* out, long total) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long idx = ((long)blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (idx >= total) return;
-  out[idx] = act[idx] > 0.f ? d[idx] : 0.f;
+  float a[V], b[V];
+  ldv<V>(d + idx, a);
+  ldv<V>(act + idx, b);
+#pragma unroll
+  for (int e = 0; e < V; ++e) a[e] = b[e] > 0.f ? a[e] : 0.f;
+  stv<V>(out + idx, a);
 }
+template <int V>
 __global__ void k_add(float* a, const float* b, long total) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < total) a[idx] += b[idx];
+  const long idx = ((long)blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (idx >= total) return;
+  float x[V], y[V];
+  ldv<V>(a + idx, x);
+  ldv<V>(b + idx, y);
+#pragma unroll
+  for (int e = 0; e < V; ++e) x[e] += y[e];
+  stv<V>(a + idx, x);
 }
 __global__ void k_bf16_to_f32(const __nv_bfloat16* a, float* out, long total) {
-  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < total) out[idx] = __bfloat162float(a[idx]);
+  const long idx = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (idx + 4 <= total && ((total & 3) == 0) && ((uintptr_t)a & 7) == 0) {
+    const uint2 u = *(const uint2*)(a + idx);
+    *(float4*)(out + idx) = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+  } else {
+    for (long i = idx; i < min(idx + 4, total); ++i) out[i] = __bfloat162float(a[i]);
+  }
 }
 
 }  // namespace
@@ -1485,6 +1632,20 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   const size_t n0 = (size_t)H * W;
   cudaStream_t st = a.stream;
   const float* P = a.params;
+  // elementwise launches: 4 elements per thread where the plane (or the
+  // whole tensor) holds a multiple of 4
+  auto plane_launch = [&](long tot, long n, auto k4, auto k1, auto... args) {
+    if (n % 4 == 0)
+      k4<<<dim3(cdiv(n / 4, kT), (unsigned)std::min(tot / n, 65535L)), kT, 0, st>>>(args...);
+    else
+      k1<<<gridp(tot, n), kT, 0, st>>>(args...);
+  };
+  auto lin_launch = [&](long tot, auto k4, auto k1, auto... args) {
+    if (tot % 4 == 0)
+      k4<<<cdiv(tot / 4, kT), kT, 0, st>>>(args...);
+    else
+      k1<<<cdiv(tot, kT), kT, 0, st>>>(args...);
+  };
   // per-slice partial sums of the reductions (weight gradients, channel
   // sums, batch statistics), one launch at a time
   float* part = ar.f(kPartCap);
@@ -1514,7 +1675,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   float* xin = ar.f((size_t)B * 3 * n0);
   if (run) {
     if (a.in_bf16)
-      k_bf16_to_f32<<<grid1((long)B * 3 * n0), kT, 0, st>>>((const __nv_bfloat16*)a.in, xin, (long)B * 3 * n0);
+      k_bf16_to_f32<<<cdiv((long)B * 3 * n0, 4 * kT), kT, 0, st>>>((const __nv_bfloat16*)a.in, xin, (long)B * 3 * n0);
     else
       cudaMemcpyAsync(xin, a.in, sizeof(float) * B * 3 * n0, cudaMemcpyDeviceToDevice, st);
   }
@@ -1582,6 +1743,16 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       return;
     }
     if (g == Ci && g == Co && s == 1 && p == (k - 1) / 2 && (k == 1 || k == 3)) {
+      if (wd % 4 == 0) {
+        const dim3 grid(cdiv((long)h * wd / 4, kT), Ci, B);
+        if (k == 1)
+          k_dw4<1, false><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+        else if (tr)
+          k_dw4<3, true><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+        else
+          k_dw4<3, false><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
+        return;
+      }
       const dim3 grid(cdiv((long)h * wd, kT), Ci, B);
       if (k == 1)
         k_dw<1, false><<<grid, kT, 0, st>>>(x, w, bias, y, Ci, h, wd, 0);
@@ -1605,8 +1776,8 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   batch_stats(su, 8, (int)n0, C.stem_m, C.stem_v);
   if (run) {
     long n = (long)B * 8 * n0;
-    k_bn<<<gridp(n, n0), kT, 0, st>>>(su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v, planes(n, n0),
-                                      8, (int)n0, 1);
+    plane_launch(n, (long)n0, k_bn<4>, k_bn<1>, su, a0, P + C.stem_g, P + C.stem_b, Q + C.stem_m, Q + C.stem_v,
+                 planes(n, n0), 8, (int)n0, 1);
   }
   BlkTape T[6];
   const float* cur = a0;
@@ -1636,9 +1807,9 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     batch_stats(t.t2, ci, (int)n, C.m2[b], C.v2[b]);
     batch_stats(t.x, ci, (int)n, C.m3[b], C.v3[b]);
     if (run)
-      k_stage1<<<gridp((long)B * ci * n, n), kT, 0, st>>>(
-          t.t1, t.t2, t.x, t.x1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
-          bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), B * ci, ci, (int)n);
+      plane_launch((long)B * ci * n, (long)n, k_stage1<4>, k_stage1<1>, t.t1, t.t2, t.x, t.x1,
+                   bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), bnp(C.g2[b], C.b2[b], C.m2[b], C.v2[b]),
+                   bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), B * ci, ci, (int)n);
     if (enc) {
       conv(t.x1, P + C.w2[b], nullptr, t.u, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
       conv(t.x, P + C.rw[b], P + C.rb[b], t.r, ci, h, w, co, 3, 2, 1, 1, false, t.H2, t.W2);
@@ -1649,12 +1820,12 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     batch_stats(t.u, co, (int)n2, C.m[b], C.v[b]);
     if (run) {
       long tot = (long)B * co * n2;
-      k_stage2<<<gridp(tot, n2), kT, 0, st>>>(t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), planes(tot, n2), co,
-                                              (int)n2);
+      plane_launch(tot, (long)n2, k_stage2<4>, k_stage2<1>, t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]),
+                   planes(tot, n2), co, (int)n2);
       k_gap<<<B * co, kT, 0, st>>>(t.y, t.g, (int)n2);
       k_eca_s<<<cdiv(B * co, kT), kT, 0, st>>>(t.g, P + C.eca[b], t.s, B, co);
       const float* skip = b == 3 ? T[1].out : b == 4 ? T[0].out : nullptr;
-      k_scale<<<gridp(tot, n2), kT, 0, st>>>(t.y, t.s, skip, t.out, planes(tot, n2), (int)n2);
+      plane_launch(tot, (long)n2, k_scale<4>, k_scale<1>, t.y, t.s, skip, t.out, planes(tot, n2), (int)n2);
     }
     cur = t.out;
     h = t.H2;
@@ -1800,6 +1971,16 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       return;
     }
     if (g == Ci && g == Co && s == 1 && p == (k - 1) / 2 && (k == 1 || k == 3)) {
+      if (ww % 4 == 0) {
+        const dim3 grid(cdiv((long)hh * ww / 4, kT), Ci, B);
+        if (k == 1)
+          k_dw4<1, false><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+        else if (tr)
+          k_dw4<3, false><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+        else
+          k_dw4<3, true><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
+        return;
+      }
       const dim3 grid(cdiv((long)hh * ww, kT), Ci, B);
       if (k == 1)
         k_dw<1, false><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, Ci, hh, ww, 1);
@@ -1832,10 +2013,10 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
                    int accumulate) {
     if (!run) return;
     if (a.bn_batch)
-      k_bn_dx_batch<<<gridp(tot, n), kT, 0, st>>>(d, x, bn, gacc, dgam, dbet, (double)B * n, out, planes(tot, n), Cc, n,
-                                               accumulate);
+      plane_launch(tot, (long)n, k_bn_dx_batch<4>, k_bn_dx_batch<1>, d, x, bn, gacc, dgam, dbet, (double)B * n, out,
+                   planes(tot, n), Cc, n, accumulate);
     else
-      k_bn_dx<<<gridp(tot, n), kT, 0, st>>>(d, bn, out, planes(tot, n), Cc, n, accumulate);
+      plane_launch(tot, (long)n, k_bn_dx<4>, k_bn_dx<1>, d, bn, out, planes(tot, n), Cc, n, accumulate);
   };
   // output conv
   float* dcur = ar.f((size_t)B * 8 * n0);
@@ -1867,18 +2048,19 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     const long tot2 = (long)B * co * n2, tot = (long)B * ci * n;
     float* dx = dxs[b & 1];
     if (run) {
-      if (b == 0) k_add<<<grid1(tot2), kT, 0, st>>>(dcur, dskip0, tot2);
-      if (b == 1) k_add<<<grid1(tot2), kT, 0, st>>>(dcur, dskip1, tot2);
-      if (b == 3) k_add<<<grid1(tot2), kT, 0, st>>>(dskip1, dcur, tot2);
-      if (b == 4) k_add<<<grid1(tot2), kT, 0, st>>>(dskip0, dcur, tot2);
+      if (b == 0) lin_launch(tot2, k_add<4>, k_add<1>, dcur, dskip0, tot2);
+      if (b == 1) lin_launch(tot2, k_add<4>, k_add<1>, dcur, dskip1, tot2);
+      if (b == 3) lin_launch(tot2, k_add<4>, k_add<1>, dskip1, dcur, tot2);
+      if (b == 4) lin_launch(tot2, k_add<4>, k_add<1>, dskip0, dcur, tot2);
       // ECA
       k_eca_ds<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
       k_eca_back<<<cdiv(B, 64), 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
       reduce(dkp, B, 3, 1, 0, C.eca[b]);
-      k_eca_dy<<<gridp(tot2, n2), kT, 0, st>>>(dcur, t.s, dgm, dy, planes(tot2, n2), n2);
+      plane_launch(tot2, (long)n2, k_eca_dy<4>, k_eca_dy<1>, dcur, t.s, dgm, dy, planes(tot2, n2), n2);
       // main branch: dbn = dy [BN(u) > 0]; du = dbn gam / sigma
       BnP bn = bnp(C.g[b], C.be[b], C.m[b], C.v[b]);
-      k_relu_bn_mask<<<gridp(tot2, n2), kT, 0, st>>>(dy, t.u, bn, dtmp, planes(tot2, n2), co, n2);
+      plane_launch(tot2, (long)n2, k_relu_bn_mask<4>, k_relu_bn_mask<1>, dy, t.u, bn, dtmp, planes(tot2, n2), co,
+                   n2);
     }
     chan(dtmp, t.u, Q + C.m[b], Q + C.v[b], co, n2, C.g[b], C.be[b]);
     bn_dx(dtmp, t.u, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), C.g[b], C.be[b], dtmp, tot2, co, n2, 0);
@@ -1894,7 +2076,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     chan(dy, nullptr, nullptr, nullptr, co, n2, -1, C.rb[b]);
     dgrad(dy, P + C.rw[b], dx, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2);
     // stage 1: dv = dx1 [x1 > 0]
-    if (run) k_relu_mask<<<grid1(tot), kT, 0, st>>>(dx1, t.x1, dx1, tot);
+    if (run) lin_launch(tot, k_relu_mask<4>, k_relu_mask<1>, dx1, t.x1, dx1, tot);
     chan(dx1, t.t1, Q + C.m1[b], Q + C.v1[b], ci, n, C.g1[b], C.b1[b]);
     chan(dx1, t.t2, Q + C.m2[b], Q + C.v2[b], ci, n, C.g2[b], C.b2[b]);
     chan(dx1, t.x, Q + C.m3[b], Q + C.v3[b], ci, n, C.g3[b], C.b3[b]);
@@ -1910,7 +2092,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   }
   // stem: a0 = ReLU(BN(su))
   const long tot0 = (long)B * 8 * n0;
-  if (run) k_relu_mask<<<grid1(tot0), kT, 0, st>>>(dcur, a0, dtmp, tot0);
+  if (run) lin_launch(tot0, k_relu_mask<4>, k_relu_mask<1>, dcur, a0, dtmp, tot0);
   chan(dtmp, su, Q + C.stem_m, Q + C.stem_v, 8, (int)n0, C.stem_g, C.stem_b);
   bn_dx(dtmp, su, bnp(C.stem_g, C.stem_b, C.stem_m, C.stem_v), C.stem_g, C.stem_b, dtmp, tot0, 8, (int)n0, 0);
   wgrad(xin, dtmp, 3, H, W, 8, 3, 1, 1, 1, false, H, W, C.stem_w);
