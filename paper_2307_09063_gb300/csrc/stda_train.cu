@@ -58,6 +58,31 @@ Slices slices(long total, long width, long outputs, int align, int blocks_per_sm
   return Slices{(int)S, (int)cdiv(total, S)};
 }
 
+// The elementwise kernels take V = 4 consecutive elements per thread
+// (16-byte loads and stores; the plane size is then a multiple of 4) or V = 1.
+template <int V>
+__device__ __forceinline__ void ldv(const float* p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 f = *(const float4*)p;
+    v[0] = f.x;
+    v[1] = f.y;
+    v[2] = f.z;
+    v[3] = f.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = p[e];
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float (&v)[V]) {
+  if constexpr (V == 4) {
+    *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) p[e] = v[e];
+  }
+}
+
 // ----------------------------------------------------------- forward ops
 // Each thread computes NT consecutive output channels (forward) or input
 // channels (input gradient) of one pixel, so every activation load feeds NT
@@ -281,6 +306,62 @@ __global__ void __launch_bounds__(256) k_dw4(const float* __restrict__ src, cons
     acc[3] += o.w;
   }
   *(float4*)dp = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+// Full 3x3 stride-1 pad-1 convs of few channels (the stem 3 -> 8, the output
+// conv 8 -> 1) and their input gradients, four horizontally adjacent pixels
+// per thread (W a multiple of 4): dst[n][Y][X] (+)= bias[n] + sum_{m,ky,kx}
+// W(n, m, ky, kx) src[m][Y + d ky - d][X + d kx - d], d = -1 when FLIP (the
+// input gradient of a conv), W(n, m) = w[n][m] or, when WT, w[m][n].
+template <int M, int N, bool FLIP, bool WT>
+__global__ void __launch_bounds__(256) k_cs1(const float* __restrict__ src, const float* __restrict__ w,
+                                             const float* __restrict__ bias, float* __restrict__ dst, int H, int W,
+                                             int accumulate) {
+  __shared__ float ws[M * N * 9];
+  for (int i = threadIdx.x; i < M * N * 9; i += blockDim.x) ws[i] = w[i];
+  __syncthreads();
+  const int W4 = W >> 2, q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H * W4) return;
+  const int Y = q / W4, X0 = (q - Y * W4) * 4, b = blockIdx.y;
+  const size_t plane = (size_t)H * W;
+  float acc[N][4];
+#pragma unroll
+  for (int n = 0; n < N; ++n)
+#pragma unroll
+    for (int o = 0; o < 4; ++o) acc[n][o] = bias ? bias[n] : 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float* sp = src + ((size_t)b * M + m) * plane;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const int sy = FLIP ? Y + 1 - ky : Y - 1 + ky;
+      if ((unsigned)sy >= (unsigned)H) continue;
+      const float* row = sp + (size_t)sy * W + X0;
+      const float4 c4 = *(const float4*)row;
+      const float v[6] = {X0 > 0 ? row[-1] : 0.f, c4.x, c4.y, c4.z, c4.w, X0 + 4 < W ? row[4] : 0.f};
+#pragma unroll
+      for (int n = 0; n < N; ++n)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const float wv = ws[(WT ? m * N + n : n * M + m) * 9 + ky * 3 + kx];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) acc[n][o] += v[o + (FLIP ? 2 - kx : kx)] * wv;
+        }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    float* dp = dst + ((size_t)b * N + n) * plane + (size_t)Y * W + X0;
+    float4 r = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
+    if (accumulate) {
+      const float4 o = *(const float4*)dp;
+      r.x += o.x;
+      r.y += o.y;
+      r.z += o.z;
+      r.w += o.w;
+    }
+    *(float4*)dp = r;
+  }
 }
 
 // Weight gradients of the stride-1, pad (K - 1) / 2 convs: the per-channel
@@ -1147,6 +1228,7 @@ __global__ void k_wgrad(const float* __restrict__ x, const float* __restrict__ d
 // Per-channel sums over one slice (pixels [chunk S, chunk S + S) of the B n):
 // S1 = sum a, S2 = sum a (v - mean) / sqrt(var + eps) (S2 only if v);
 // part[chunk][c][2].
+template <int V>
 __global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict__ v, const float* __restrict__ mean,
                             const float* __restrict__ var, float* __restrict__ part, int B, int C, int n, int S) {
   __shared__ float sh[32];
@@ -1158,10 +1240,15 @@ __global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict
     const float* ap = a + ((size_t)b * C + c) * n;
     const float* vp = v ? v + ((size_t)b * C + c) * n : nullptr;
     const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      float d = ap[q];
-      s1 += d;
-      if (vp) s2 += d * (vp[q] - m) * is;
+    for (int q = q0 + V * threadIdx.x; q < q1; q += V * blockDim.x) {
+      float d[V], u[V];
+      ldv<V>(ap + q, d);
+      if (vp) ldv<V>(vp + q, u);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        s1 += d[e];
+        if (vp) s2 += d[e] * (u[e] - m) * is;
+      }
     }
   }
   float r1 = block_sum(s1, sh);
@@ -1212,31 +1299,6 @@ __global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ part, 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, int n) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[j] = (float)a[j];
-}
-
-// The elementwise kernels take V = 4 consecutive elements per thread
-// (16-byte loads and stores; the plane size is then a multiple of 4) or V = 1.
-template <int V>
-__device__ __forceinline__ void ldv(const float* p, float (&v)[V]) {
-  if constexpr (V == 4) {
-    const float4 f = *(const float4*)p;
-    v[0] = f.x;
-    v[1] = f.y;
-    v[2] = f.z;
-    v[3] = f.w;
-  } else {
-#pragma unroll
-    for (int e = 0; e < V; ++e) v[e] = p[e];
-  }
-}
-template <int V>
-__device__ __forceinline__ void stv(float* p, const float (&v)[V]) {
-  if constexpr (V == 4) {
-    *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < V; ++e) p[e] = v[e];
-  }
 }
 
 // y = relu?(gam (x - mean) / sqrt(var + eps) + bet) per channel
@@ -1303,11 +1365,17 @@ __global__ void k_stage2(const float* u, const float* r, float* y, BnP bn, int p
 }
 
 // per (b, c): g = mean over the map
+template <int V>
 __global__ void k_gap(const float* __restrict__ y, float* __restrict__ g, int n) {
   __shared__ float sh[32];
   const float* p = y + (size_t)blockIdx.x * n;
   float s = 0.f;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) s += p[q];
+  for (int q = V * threadIdx.x; q < n; q += V * blockDim.x) {
+    float v[V];
+    ldv<V>(p + q, v);
+#pragma unroll
+    for (int e = 0; e < V; ++e) s += v[e];
+  }
   float r = block_sum(s, sh);
   if (threadIdx.x == 0) g[blockIdx.x] = r / (float)n;
 }
@@ -1386,12 +1454,19 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* part, int n, doub
 
 // ---------------------------------------------------------- backward ops
 // per (b, c): ds = sum dout * y
+template <int V>
 __global__ void k_eca_ds(const float* dout, const float* y, float* ds, int n) {
   __shared__ float sh[32];
   const float* a = dout + (size_t)blockIdx.x * n;
   const float* v = y + (size_t)blockIdx.x * n;
   float s = 0.f;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) s += a[q] * v[q];
+  for (int q = V * threadIdx.x; q < n; q += V * blockDim.x) {
+    float x[V], z[V];
+    ldv<V>(a + q, x);
+    ldv<V>(v + q, z);
+#pragma unroll
+    for (int e = 0; e < V; ++e) s += x[e] * z[e];
+  }
   float r = block_sum(s, sh);
   if (threadIdx.x == 0) ds[blockIdx.x] = r;
 }
@@ -1466,6 +1541,7 @@ __global__ void k_bn_dx(const float* a, BnP bn, float* out, int planes, int C, i
 // Batch statistics of a BN input x[B][C][n]: part[chunk][c] = sum over the
 // slice's pixels (chunk S .. chunk S + S of the B n) of x (mean == null) or
 // of (x - mean[c])^2.
+template <int V>
 __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__ mean, float* __restrict__ part,
                           int B, int C, int n, int S) {
   __shared__ float sh[32];
@@ -1476,9 +1552,14 @@ __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__
   for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
     const float* p = x + ((size_t)b * C + c) * n;
     const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      const float d = p[q] - m;
-      s += mean ? d * d : p[q];
+    for (int q = q0 + V * threadIdx.x; q < q1; q += V * blockDim.x) {
+      float u[V];
+      ldv<V>(p + q, u);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const float d = u[e] - m;
+        s += mean ? d * d : u[e];
+      }
     }
   }
   const float r = block_sum(s, sh);
@@ -1664,10 +1745,11 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto batch_stats = [&](const float* x, int Cc, int n, int moff, int voff) {
     if (!run || !a.bn_batch) return;
     const double N = (double)B * n;
-    const Slices sl = slices((long)B * n, Cc, Cc, 1, kSliceBlocks);
-    k_bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, nullptr, part, B, Cc, n, sl.S);
+    const Slices sl = slices((long)B * n, Cc, Cc, 4, kSliceBlocks);
+    auto bn_part = n % 4 == 0 ? k_bn_part<4> : k_bn_part<1>;
+    bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, nullptr, part, B, Cc, n, sl.S);
     reduce(part, sl.n, Cc, 1, 0, 0, bst + moff, 1.0 / N);
-    k_bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, bst + moff, part, B, Cc, n, sl.S);
+    bn_part<<<dim3(Cc, sl.n), kT, 0, st>>>(x, bst + moff, part, B, Cc, n, sl.S);
     reduce(part, sl.n, Cc, 1, 0, 0, bst + voff, 1.0 / N);
   };
 
@@ -1736,6 +1818,15 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     if (!run) return;
     if (dense_s2(k, s, p, g, tr) && h % 2 == 0 && wd % 2 == 0) {
       dconv(tr, k, x, w, bias, y, Ci, h, wd, Co, 0);
+      return;
+    }
+    if (g == 1 && s == 1 && p == 1 && k == 3 && !tr && wd % 4 == 0 &&
+        ((Ci == 3 && Co == 8) || (Ci == 8 && Co == 1))) {
+      const dim3 grid(cdiv((long)h * wd / 4, kT), B);
+      if (Ci == 3)
+        k_cs1<3, 8, false, false><<<grid, kT, 0, st>>>(x, w, bias, y, h, wd, 0);
+      else
+        k_cs1<8, 1, false, false><<<grid, kT, 0, st>>>(x, w, bias, y, h, wd, 0);
       return;
     }
     if (dense_s2(k, s, p, g, tr)) {
@@ -1822,7 +1913,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       long tot = (long)B * co * n2;
       plane_launch(tot, (long)n2, k_stage2<4>, k_stage2<1>, t.u, t.r, t.y, bnp(C.g[b], C.be[b], C.m[b], C.v[b]),
                    planes(tot, n2), co, (int)n2);
-      k_gap<<<B * co, kT, 0, st>>>(t.y, t.g, (int)n2);
+      (n2 % 4 == 0 ? k_gap<4> : k_gap<1>)<<<B * co, kT, 0, st>>>(t.y, t.g, (int)n2);
       k_eca_s<<<cdiv(B * co, kT), kT, 0, st>>>(t.g, P + C.eca[b], t.s, B, co);
       const float* skip = b == 3 ? T[1].out : b == 4 ? T[0].out : nullptr;
       plane_launch(tot, (long)n2, k_scale<4>, k_scale<1>, t.y, t.s, skip, t.out, planes(tot, n2), (int)n2);
@@ -1966,6 +2057,15 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       dconv(!tr, k, dy, w, nullptr, dx, Co, Ho, Wo, Ci, 1);
       return;
     }
+    if (g == 1 && s == 1 && p == 1 && k == 3 && !tr && ww % 4 == 0 &&
+        ((Ci == 3 && Co == 8) || (Ci == 8 && Co == 1))) {
+      const dim3 grid(cdiv((long)hh * ww / 4, kT), B);
+      if (Ci == 3)
+        k_cs1<8, 3, true, true><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, hh, ww, 1);
+      else
+        k_cs1<1, 8, true, true><<<grid, kT, 0, st>>>(dy, w, nullptr, dx, hh, ww, 1);
+      return;
+    }
     if (dense_s2(k, s, p, g, tr)) {
       igemm(tr ? DEC_DGRAD : ENC_DGRAD, dy, w, nullptr, dx, Co, Ho, Wo, Ci, hh, ww);
       return;
@@ -2002,8 +2102,9 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto chan = [&](const float* av, const float* v, const float* mean, const float* var, int Cc, int n,
                   int dgam, int dbet) {
     if (!run) return;
-    const Slices sl = slices((long)B * n, Cc, 2L * Cc, 1, kSliceBlocks);
-    k_chan_sums<<<dim3(Cc, sl.n), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n, sl.S);
+    const Slices sl = slices((long)B * n, Cc, 2L * Cc, 4, kSliceBlocks);
+    (n % 4 == 0 ? k_chan_sums<4> : k_chan_sums<1>)<<<dim3(Cc, sl.n), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n,
+                                                                                 sl.S);
     if (dbet >= 0) reduce(part, sl.n, Cc, 2, 0, dbet);
     if (dgam >= 0) reduce(part, sl.n, Cc, 2, 1, dgam);
   };
@@ -2053,7 +2154,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       if (b == 3) lin_launch(tot2, k_add<4>, k_add<1>, dskip1, dcur, tot2);
       if (b == 4) lin_launch(tot2, k_add<4>, k_add<1>, dskip0, dcur, tot2);
       // ECA
-      k_eca_ds<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
+      (n2 % 4 == 0 ? k_eca_ds<4> : k_eca_ds<1>)<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
       k_eca_back<<<cdiv(B, 64), 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
       reduce(dkp, B, 3, 1, 0, C.eca[b]);
       plane_launch(tot2, (long)n2, k_eca_dy<4>, k_eca_dy<1>, dcur, t.s, dgm, dy, planes(tot2, n2), n2);
