@@ -1296,6 +1296,30 @@ __global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ part, 
   }
 }
 
+// The same for few outputs: one warp per output j (of n), its lanes summing
+// chunks lane, lane + 32, ... in order, then a fixed shuffle tree. With
+// dst_odd >= 0 the partials are [chunk][n / 2][2] pairs: even j go to
+// acc[dst + j / 2], odd j to acc[dst_odd + j / 2].
+__global__ void __launch_bounds__(256) k_reduce_few(const float* __restrict__ part, int nchunks, int n, int stride,
+                                                    int off, double* __restrict__ acc, long dst, long dst_odd,
+                                                    float* __restrict__ fout, double scale) {
+  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const float* src = part + (size_t)j * stride + off;
+  const size_t cs = (size_t)n * stride;
+  double s = 0.0;
+  for (int c = lane; c < nchunks; c += 32) s += (double)src[c * cs];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane) return;
+  if (fout)
+    fout[j] = (float)(s * scale);
+  else if (dst_odd >= 0)
+    acc[((j & 1) ? dst_odd : dst) + (j >> 1)] += s;
+  else
+    acc[dst + j] += s;
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, int n) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[j] = (float)a[j];
@@ -1735,7 +1759,10 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   // writes fout[j] = scale * that sum)
   auto reduce = [&](const float* pp, int nch, int n, int stride, int off, long dst, float* fout = nullptr,
                     double scale = 1.0) {
-    k_reduce<<<cdiv(n, 32), 256, 0, st>>>(pp, nch, n, stride, off, gacc, dst, fout, scale);
+    if (n <= 1024)
+      k_reduce_few<<<cdiv(n, 8), 256, 0, st>>>(pp, nch, n, stride, off, gacc, dst, -1, fout, scale);
+    else
+      k_reduce<<<cdiv(n, 32), 256, 0, st>>>(pp, nch, n, stride, off, gacc, dst, fout, scale);
   };
   // BN statistics: the running ones, or (training mode) the batch's, computed
   // into `bst` (same layout as the running buffers) right before each BN
@@ -2105,8 +2132,12 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     const Slices sl = slices((long)B * n, Cc, 2L * Cc, 4, kSliceBlocks);
     (n % 4 == 0 ? k_chan_sums<4> : k_chan_sums<1>)<<<dim3(Cc, sl.n), kT, 0, st>>>(av, v, mean, var, part, B, Cc, n,
                                                                                  sl.S);
-    if (dbet >= 0) reduce(part, sl.n, Cc, 2, 0, dbet);
-    if (dgam >= 0) reduce(part, sl.n, Cc, 2, 1, dgam);
+    if (dbet >= 0 && dgam >= 0)  // both sums in one launch
+      k_reduce_few<<<cdiv(2 * Cc, 8), 256, 0, st>>>(part, sl.n, 2 * Cc, 1, 0, gacc, dbet, dgam, nullptr, 1.0);
+    else if (dbet >= 0)
+      reduce(part, sl.n, Cc, 2, 0, dbet);
+    else if (dgam >= 0)
+      reduce(part, sl.n, Cc, 2, 1, dgam);
   };
   // out (+)= dBN input: gam / sigma dy (running statistics), or the batch
   // adjoint, whose sums of this BN chan() has just added to gacc
