@@ -1600,7 +1600,8 @@ __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const dou
     const int c = pl % C;
     const size_t idx = (size_t)pl * n + q;
     const float is = rsqrtf(bn.v[c] + 1e-5f), m = bn.m[c], g = bn.g[c] * is;
-    const double sb = gacc[dbet + c], sg = gacc[dgam + c];
+    // (sum dy + xhat sum dy xhat) / N as cb + xhat cg, the two channel means in FP32
+    const float cb = (float)(gacc[dbet + c] / N), cg = (float)(gacc[dgam + c] / N);
     float d[V], xv[V], o[V];
     ldv<V>(dy + idx, d);
     ldv<V>(x + idx, xv);
@@ -1608,8 +1609,7 @@ __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const dou
 #pragma unroll
     for (int e = 0; e < V; ++e) {
       const float xh = (xv[e] - m) * is;
-      const float corr = (float)((sb + (double)xh * sg) / N);
-      const float v = g * (d[e] - corr);
+      const float v = g * (d[e] - (cb + xh * cg));
       d[e] = accumulate ? o[e] + v : v;
     }
     stv<V>(out + idx, d);
