@@ -1494,25 +1494,33 @@ __global__ void k_eca_ds(const float* dout, const float* y, float* ds, int n) {
   float r = block_sum(s, sh);
   if (threadIdx.x == 0) ds[blockIdx.x] = r;
 }
-// per window b (one thread per b): dz = ds s (1 - s); dk partial; dg
+// per window b (one block, thread = channel c < C <= 64): dz = ds s (1 - s);
+// dg[c] = sum_j dz[c + 1 - j] k3[j] / n (the mean's adjoint); dk partial
+// dk[j] = sum_c dz[c] g[c + j - 1], summed over the block in a fixed order
 __global__ void k_eca_back(const float* ds, const float* sc, const float* g, const float* k3, float* dgm,
                            float* dk_part, int B, int C, int n) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  const float *dsb = ds + b * C, *sb = sc + b * C, *gb = g + b * C;
-  float* dg = dgm + b * C;
-  float dk[3] = {0.f, 0.f, 0.f};
-  for (int c = 0; c < C; ++c) dg[c] = 0.f;
-  for (int c = 0; c < C; ++c) {
-    float dz = dsb[c] * sb[c] * (1.f - sb[c]);
-    for (int j = 0; j < 3; ++j) {
-      int cc = c + j - 1;
-      if (cc < 0 || cc >= C) continue;
-      dk[j] += dz * gb[cc];
-      dg[cc] += dz * k3[j] / (float)n;
-    }
+  __shared__ float dz[64];
+  __shared__ float sh[32];
+  const int b = blockIdx.x, c = threadIdx.x;
+  if (c < C) {
+    const float s = sc[b * C + c];
+    dz[c] = ds[b * C + c] * s * (1.f - s);
   }
-  for (int j = 0; j < 3; ++j) dk_part[b * 3 + j] = dk[j];
+  __syncthreads();
+  if (c < C) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int cc = c + 1 - j;
+      if (cc >= 0 && cc < C) v += dz[cc] * k3[j];
+    }
+    dgm[b * C + c] = v / (float)n;
+  }
+  for (int j = 0; j < 3; ++j) {
+    const int cg = c + j - 1;
+    const float t = block_sum(c < C && cg >= 0 && cg < C ? dz[c] * g[b * C + cg] : 0.f, sh);
+    if (c == 0) dk_part[b * 3 + j] = t;
+  }
 }
 // dy = s * dout + dg (the mean's adjoint, already divided by n)
 template <int V>
@@ -1590,10 +1598,11 @@ __global__ void k_bn_part(const float* __restrict__ x, const float* __restrict__
   if (threadIdx.x == 0) part[(size_t)chunk * C + c] = r;
 }
 // Batch-statistics BN adjoint: out (+)= gam / sigma (dy - (sum dy + xhat sum
-// dy xhat) / N), the two sums of this BN being gacc[dbet + c], gacc[dgam + c].
+// dy xhat) / N), the two sums of this BN being gacc[dbet + c], gacc[dgam + c];
+// invN = 1 / N.
 template <int V>
 __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const double* __restrict__ gacc, long dgam,
-                              long dbet, double N, float* out, int planes, int C, int n, int accumulate) {
+                              long dbet, float invN, float* out, int planes, int C, int n, int accumulate) {
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   if (q >= n) return;
   for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
@@ -1601,7 +1610,7 @@ __global__ void k_bn_dx_batch(const float* dy, const float* x, BnP bn, const dou
     const size_t idx = (size_t)pl * n + q;
     const float is = rsqrtf(bn.v[c] + 1e-5f), m = bn.m[c], g = bn.g[c] * is;
     // (sum dy + xhat sum dy xhat) / N as cb + xhat cg, the two channel means in FP32
-    const float cb = (float)(gacc[dbet + c] / N), cg = (float)(gacc[dgam + c] / N);
+    const float cb = (float)gacc[dbet + c] * invN, cg = (float)gacc[dgam + c] * invN;
     float d[V], xv[V], o[V];
     ldv<V>(dy + idx, d);
     ldv<V>(x + idx, xv);
@@ -2145,8 +2154,8 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
                    int accumulate) {
     if (!run) return;
     if (a.bn_batch)
-      plane_launch(tot, (long)n, k_bn_dx_batch<4>, k_bn_dx_batch<1>, d, x, bn, gacc, dgam, dbet, (double)B * n, out,
-                   planes(tot, n), Cc, n, accumulate);
+      plane_launch(tot, (long)n, k_bn_dx_batch<4>, k_bn_dx_batch<1>, d, x, bn, gacc, dgam, dbet,
+                   (float)(1.0 / ((double)B * n)), out, planes(tot, n), Cc, n, accumulate);
     else
       plane_launch(tot, (long)n, k_bn_dx<4>, k_bn_dx<1>, d, bn, out, planes(tot, n), Cc, n, accumulate);
   };
@@ -2186,7 +2195,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       if (b == 4) lin_launch(tot2, k_add<4>, k_add<1>, dskip0, dcur, tot2);
       // ECA
       (n2 % 4 == 0 ? k_eca_ds<4> : k_eca_ds<1>)<<<B * co, kT, 0, st>>>(dcur, t.y, ds, n2);
-      k_eca_back<<<cdiv(B, 64), 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
+      k_eca_back<<<B, 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
       reduce(dkp, B, 3, 1, 0, C.eca[b]);
       plane_launch(tot2, (long)n2, k_eca_dy<4>, k_eca_dy<1>, dcur, t.s, dgm, dy, planes(tot2, n2), n2);
       // main branch: dbn = dy [BN(u) > 0]; du = dbn gam / sigma
