@@ -65,6 +65,7 @@ def test_null_arguments_rejected_without_gpu(L):
     assert lib.stda_create(None, None) == L.ERR_INVALID_ARG
     assert lib.stda_destroy(None) == L.ERR_INVALID_ARG
     assert lib.stda_forward(None, None, None, 1, 8, 8, None) == L.ERR_INVALID_ARG
+    assert lib.stda_forward_host(None, None, None, 1, 8, 8, None) == L.ERR_INVALID_ARG
     assert lib.stda_init_params(0, None, None) == L.ERR_INVALID_ARG
     cfg = L.Config(12, 16, 1, 0, 0, 0)  # H not a multiple of 8
     h = ctypes.c_void_p()
