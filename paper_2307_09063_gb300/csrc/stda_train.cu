@@ -466,16 +466,31 @@ __global__ void __launch_bounds__(256) k_wgrad_s1(const float* __restrict__ A, c
 //     out[n][Y][X] (+)= bias[n] + sum w[m][n][ky][kx] src[m][yi][xi] over Y = 2yi-1+ky, X = 2xi-1+kx
 // Stages are copied with cp.async (zero-filled outside the source) into two
 // shared-memory buffers, the next stage in flight while the current one is
-// used. 256 threads: warp w = (row group or output phase, channel group);
+// used; the weights come re-laid as wT[m][ky kx][n] (k_wt), 16 bytes a copy,
+// as do the transposed form's source rows. 256 threads: warp w = (row group or output phase, channel group);
 // lane = (row in the warp, column), TX columns per warp row. Sums run in FP32
 // over m, then ky, kx.
 constexpr int kDcMC = 4;  // source channels per stage
+constexpr long kDcWT = 32768;  // largest dense conv weight tensor (64 x 32 x 4 x 4)
 
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0) : "memory");
 }
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Weights of a dense conv re-laid as wT[m][ky kx][n] (m source, n output
+// channel), so a block's output channels of one (m, tap) are contiguous:
+// from w[m][n][t] (T) or w[n][m][t].
+__global__ void k_wt(const float* __restrict__ w, float* __restrict__ wT, int M, int N, int KK, int T) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * KK * N) return;
+  const int n = e % N, t = (e / N) % KK, m = e / (N * KK);
+  wT[e] = T ? w[((size_t)m * N + n) * KK + t] : w[((size_t)n * M + m) * KK + t];
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -527,10 +542,10 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
                 ok ? sb + (size_t)(m0 + m) * splane + (size_t)gy * Ws + gx : src, ok);
     }
     float* wsb = buf + G::NX;
-    for (int e = tid; e < G::NW; e += 256) {
-      const int nl = e % NB, t = (e / NB) % KK, m = e / (NB * KK), n = n0 + nl;
-      const bool ok = n < N && m0 + m < M;
-      cp_async4(wsb + e, ok ? w + ((size_t)n * M + m0 + m) * KK + t : w, ok);
+    for (int e = tid; e < G::NW / 4; e += 256) {  // 16-byte runs of wT[m][t][n0 ..]
+      const int q = e % (NB / 4), t = (e / (NB / 4)) % KK, m = e / ((NB / 4) * KK);
+      const bool ok = m0 + m < M;
+      cp_async16(wsb + (m * KK + t) * NB + 4 * q, ok ? w + ((size_t)(m0 + m) * KK + t) * N + n0 + 4 * q : w, ok);
     }
     cp_async_commit();
   };
@@ -588,7 +603,7 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
 template <int K, int NO, int TX, int NPP>
 struct StconvGeo {
   static constexpr int NP = NPP, KK = K * K, RW = 32 / TX, TU = NP * RW, R = TU + 2;
-  static constexpr int RS = TX == 32 ? 34 : 48;  // source tile row (TX + 2, padded against conflicts)
+  static constexpr int RS = TX == 32 ? 40 : 48;  // source tile row (TX + 8, padded against conflicts)
   static constexpr int CS = R * RS, NB = 2 * NO;
   static constexpr int NX = kDcMC * CS, NW = kDcMC * KK * NB, STAGE = NX + NW;
   static constexpr size_t smem() { return sizeof(float) * 2 * STAGE; }
@@ -636,17 +651,21 @@ __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, c
   const size_t splane = (size_t)Hs * Ws;
   const float* sb = src + (size_t)b * M * splane;
   auto issue = [&](int m0, float* buf) {
-    for (int e = tid; e < G::NX; e += 256) {
-      const int m = e / (R * RS), r = (e / RS) % R, c = e % RS;
-      const int gy = U0 - 1 + r, gx = V0 - 1 + c;
-      const bool ok = m0 + m < M && c < TX + 2 && (unsigned)gy < (unsigned)Hs && (unsigned)gx < (unsigned)Ws;
-      cp_async4(buf + e, ok ? sb + (size_t)(m0 + m) * splane + (size_t)gy * Ws + gx : src, ok);
+    // tile row r, column c holds source (U0 - 1 + r, V0 - 4 + c): 16-byte
+    // runs that lie wholly inside or outside the map (Ws, V0 multiples of 4)
+    constexpr int CH = (TX + 8) / 4;
+    for (int e = tid; e < kDcMC * R * CH; e += 256) {
+      const int j = e % CH, r = (e / CH) % R, m = e / (CH * R);
+      const int gy = U0 - 1 + r, gx = V0 - 4 + 4 * j;
+      const bool ok = m0 + m < M && (unsigned)gy < (unsigned)Hs && (unsigned)gx < (unsigned)Ws;
+      cp_async16(buf + m * G::CS + r * RS + 4 * j, ok ? sb + (size_t)(m0 + m) * splane + (size_t)gy * Ws + gx : src,
+                 ok);
     }
     float* wsb = buf + G::NX;
-    for (int e = tid; e < G::NW; e += 256) {
-      const int nl = e % NB, t = (e / NB) % KK, m = e / (NB * KK), n = n0 + nl;
-      const bool ok = n < N && m0 + m < M;
-      cp_async4(wsb + e, ok ? w + ((size_t)(m0 + m) * N + n) * KK + t : w, ok);
+    for (int e = tid; e < G::NW / 4; e += 256) {  // 16-byte runs of wT[m][t][n0 ..]
+      const int q = e % (NB / 4), t = (e / (NB / 4)) % KK, m = e / ((NB / 4) * KK);
+      const bool ok = m0 + m < M;
+      cp_async16(wsb + (m * KK + t) * NB + 4 * q, ok ? w + ((size_t)(m0 + m) * KK + t) * N + n0 + 4 * q : w, ok);
     }
     cp_async_commit();
   };
@@ -667,7 +686,7 @@ __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, c
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* xb = xs + ru * RS + v;
+    const float* xb = xs + ru * RS + v + 3;  // + 1 + dx: column V0 + v + dx
     const float* wb = ws + cg * NO;
     switch (ph) {
       case 0: stconv_phase<K, NO, TX, NP, 0, 0>(xb, wb, acc); break;
@@ -1818,8 +1837,16 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   };
   auto dense_s2 = [](int k, int s, int p, int g, bool tr) { return g == 1 && s == 2 && p == 1 && k == (tr ? 4 : 3); };
   // direct stride-2 conv (T: transposed) of src [B][M][Hs][Ws] into N channels
+  float* wT = ar.f(kDcWT);  // a dense conv's weights as [m][tap][n]
+  // the direct form applies: N a multiple of the block's channels, even maps,
+  // and for the transposed form a source width that is a multiple of 4
+  auto dconv_ok = [](bool T, int M, int Hs, int Ws, int N, int K) {
+    const int no = N >= 32 ? 16 : N >= 16 ? 8 : 4;
+    return N % (2 * no) == 0 && Hs % 2 == 0 && Ws % 2 == 0 && (!T || Ws % 4 == 0) && (long)M * N * K * K <= kDcWT;
+  };
   auto dconv = [&](bool T, int K, const float* src, const float* w, const float* bias, float* out, int M, int Hs,
                    int Ws, int N, int accumulate) {
+    k_wt<<<cdiv((long)M * K * K * N, kT), kT, 0, st>>>(w, wT, M, N, K * K, T ? 1 : 0);
     const int no = N >= 32 ? 16 : N >= 16 ? 8 : 4;
     const int tx = (T ? Ws : Ws / 2) >= 32 ? 32 : 16;
     // pixels per thread: 2 with 16 channels; with 4 or 8 channels 4 (the
@@ -1833,7 +1860,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     const dim3 grid(tiles_for(np), cdiv(N, 2 * no), B);
     auto go = [&](auto kern, size_t smem) {
       if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<grid, 256, smem, st>>>(src, w, bias, out, M, Hs, Ws, N, accumulate);
+      kern<<<grid, 256, smem, st>>>(src, wT, bias, out, M, Hs, Ws, N, accumulate);
     };
 #define STDA_DC2(KERN, GEO, KS, NO, TX)                                                            \
   (NO < 16 && np == 4 ? go(KERN<KS, NO, TX, (NO < 16 ? 4 : 2)>, GEO<KS, NO, TX, (NO < 16 ? 4 : 2)>::smem()) \
@@ -1852,7 +1879,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto conv = [&](const float* x, const float* w, const float* bias, float* y, int Ci, int h, int wd, int Co,
                   int k, int s, int p, int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    if (dense_s2(k, s, p, g, tr) && h % 2 == 0 && wd % 2 == 0) {
+    if (dense_s2(k, s, p, g, tr) && dconv_ok(tr, Ci, h, wd, Co, k)) {
       dconv(tr, k, x, w, bias, y, Ci, h, wd, Co, 0);
       return;
     }
@@ -2088,7 +2115,7 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
   auto dgrad = [&](const float* dy, const float* w, float* dx, int Ci, int hh, int ww, int Co, int k, int s, int p,
                    int g, bool tr, int Ho, int Wo) {
     if (!run) return;
-    if (dense_s2(k, s, p, g, tr) && hh % 2 == 0 && ww % 2 == 0) {
+    if (dense_s2(k, s, p, g, tr) && dconv_ok(!tr, Co, Ho, Wo, Ci, k)) {
       // encoder: transposed 3x3 of dy; decoder: 4x4 stride-2 conv of dy
       dconv(!tr, k, dy, w, nullptr, dx, Co, Ho, Wo, Ci, 1);
       return;
