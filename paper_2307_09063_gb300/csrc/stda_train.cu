@@ -3,11 +3,16 @@
 // operation, producing dL/dtheta for all 137,915 parameters.
 //
 // The graph keeps batch normalisation unfolded (inference form with frozen
-// running statistics; gamma and beta are trained), so every tensor of the
-// taped forward is the one the adjoint needs. Tensors are NCHW float32.
-// Weight and BN gradients are first reduced per batch chunk in FP32 (one
-// thread block per (output, input) channel pair, warp shuffles), then the
-// chunks are summed in FP64 in a fixed order; the loss is an FP64 sum.
+// running statistics, or the batch's statistics in training mode; gamma and
+// beta are trained), so every tensor of the taped forward is the one the
+// adjoint needs. Tensors are NCHW float32, arithmetic FP32 on the CUDA cores:
+// dense stride-2 convs and their input gradients as direct convolutions over
+// cp.async-staged tiles, their weight gradients as split-K GEMMs, stride-1
+// depthwise / stem / output convs and their weight gradients by register
+// windows, elementwise passes four elements per thread. Weight and BN
+// gradients are first reduced over slices of the batch's pixels in FP32
+// (warp shuffles), then the slices are summed in FP64 in a fixed order; the
+// loss is an FP64 sum.
 #include <cuda_bf16.h>
 
 #include <algorithm>
