@@ -1283,6 +1283,76 @@ __global__ void k_chan_sums(const float* __restrict__ a, const float* __restrict
   }
 }
 
+// Stage 1 of a block, adjoint side, in one pass: dv = dx1 [x1 > 0] (written
+// back into dx1) and per channel over one slice of the pixels the four sums
+// S0 = sum dv and Sk = sum dv (u_k - mean_k) / sqrt(var_k + eps) for the
+// inputs u_1 = t1, u_2 = t2, u_3 = x of the three BNs (dbeta_k = S0,
+// dgamma_k = Sk); part[chunk][c][4].
+struct Bn3 {
+  const float *m1, *v1, *m2, *v2, *m3, *v3;
+};
+template <int V>
+__global__ void k_stage1_sums(float* __restrict__ dx1, const float* __restrict__ x1, const float* __restrict__ t1,
+                              const float* __restrict__ t2, const float* __restrict__ x, Bn3 bn,
+                              float* __restrict__ part, int B, int C, int n, int S) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x, chunk = blockIdx.y;
+  const long e0 = (long)chunk * S, e1 = min((long)B * n, e0 + S);
+  const float m1 = bn.m1[c], i1 = rsqrtf(bn.v1[c] + 1e-5f), m2 = bn.m2[c], i2 = rsqrtf(bn.v2[c] + 1e-5f);
+  const float m3 = bn.m3[c], i3 = rsqrtf(bn.v3[c] + 1e-5f);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
+    const size_t base = ((size_t)b * C + c) * n;
+    const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+    for (int q = q0 + V * threadIdx.x; q < q1; q += V * blockDim.x) {
+      float d[V], a[V], u1[V], u2[V], u3[V];
+      ldv<V>(dx1 + base + q, d);
+      ldv<V>(x1 + base + q, a);
+      ldv<V>(t1 + base + q, u1);
+      ldv<V>(t2 + base + q, u2);
+      ldv<V>(x + base + q, u3);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        d[e] = a[e] > 0.f ? d[e] : 0.f;
+        s0 += d[e];
+        s1 += d[e] * (u1[e] - m1) * i1;
+        s2 += d[e] * (u2[e] - m2) * i2;
+        s3 += d[e] * (u3[e] - m3) * i3;
+      }
+      stv<V>(dx1 + base + q, d);
+    }
+  }
+  const float r0 = block_sum(s0, sh), r1 = block_sum(s1, sh), r2 = block_sum(s2, sh), r3 = block_sum(s3, sh);
+  if (threadIdx.x == 0) {
+    float* o = part + ((size_t)chunk * C + c) * 4;
+    o[0] = r0;
+    o[1] = r1;
+    o[2] = r2;
+    o[3] = r3;
+  }
+}
+// part[chunk][c][4] of k_stage1_sums summed over chunks in FP64, one warp per
+// (c, k) as k_reduce_few: S0 is added to the three dbeta, Sk to dgamma_k.
+__global__ void __launch_bounds__(256) k_reduce_stage1(const float* __restrict__ part, int nchunks, int C,
+                                                       double* __restrict__ acc, long b1, long b2, long b3, long g1,
+                                                       long g2, long g3) {
+  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= 4 * C) return;
+  double s = 0.0;
+  for (int ch = lane; ch < nchunks; ch += 32) s += (double)part[(size_t)ch * 4 * C + j];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane) return;
+  const int c = j >> 2, k = j & 3;
+  if (k == 0) {
+    acc[b1 + c] += s;
+    acc[b2 + c] += s;
+    acc[b3 + c] += s;
+  } else {
+    acc[(k == 1 ? g1 : k == 2 ? g2 : g3) + c] += s;
+  }
+}
+
 // Sums partials over chunks in FP64 and adds them into the gradient
 // accumulator, acc[dst + j] += sum_chunk part[chunk][j * stride + off], or
 // (fout) writes fout[j] = scale * that sum. 256 threads: lane = output j of a
@@ -2248,11 +2318,15 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
     wgrad(t.x, dy, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2, C.rw[b]);
     chan(dy, nullptr, nullptr, nullptr, co, n2, -1, C.rb[b]);
     dgrad(dy, P + C.rw[b], dx, ci, t.h, t.w, co, kk, 2, 1, 1, !enc, t.H2, t.W2);
-    // stage 1: dv = dx1 [x1 > 0]
-    if (run) lin_launch(tot, k_relu_mask<4>, k_relu_mask<1>, dx1, t.x1, dx1, tot);
-    chan(dx1, t.t1, Q + C.m1[b], Q + C.v1[b], ci, n, C.g1[b], C.b1[b]);
-    chan(dx1, t.t2, Q + C.m2[b], Q + C.v2[b], ci, n, C.g2[b], C.b2[b]);
-    chan(dx1, t.x, Q + C.m3[b], Q + C.v3[b], ci, n, C.g3[b], C.b3[b]);
+    // stage 1: dv = dx1 [x1 > 0] and the sums of its three BNs, one pass
+    if (run) {
+      const Slices sl = slices((long)B * n, ci, 4L * ci, 4, kSliceBlocks);
+      const Bn3 b3{Q + C.m1[b], Q + C.v1[b], Q + C.m2[b], Q + C.v2[b], Q + C.m3[b], Q + C.v3[b]};
+      (n % 4 == 0 ? k_stage1_sums<4> : k_stage1_sums<1>)<<<dim3(ci, sl.n), kT, 0, st>>>(dx1, t.x1, t.t1, t.t2, t.x,
+                                                                                      b3, part, B, ci, n, sl.S);
+      k_reduce_stage1<<<cdiv(4L * ci, 8), 256, 0, st>>>(part, sl.n, ci, gacc, C.b1[b], C.b2[b], C.b3[b], C.g1[b],
+                                                        C.g2[b], C.g3[b]);
+    }
     bn_dx(dx1, t.x, bnp(C.g3[b], C.b3[b], C.m3[b], C.v3[b]), C.g3[b], C.b3[b], dx, tot, ci, n, 1);
     // dt1 = dv gam1 / sigma1 -> dw1, dx
     bn_dx(dx1, t.t1, bnp(C.g1[b], C.b1[b], C.m1[b], C.v1[b]), C.g1[b], C.b1[b], dt, tot, ci, n, 0);
