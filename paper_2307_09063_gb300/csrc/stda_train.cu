@@ -88,6 +88,14 @@ __device__ __forceinline__ void stv(float* p, const float (&v)[V]) {
   }
 }
 
+// a BN layer: gamma, beta, and the mean and variance it normalises with
+struct BnP {
+  const float *g, *b, *m, *v;
+};
+__device__ __forceinline__ float bnv(const BnP& q, int c, float x) {
+  return q.g[c] * (x - q.m[c]) * rsqrtf(q.v[c] + 1e-5f) + q.b[c];
+}
+
 // ----------------------------------------------------------- forward ops
 // Each thread computes NT consecutive output channels (forward) or input
 // channels (input gradient) of one pixel, so every activation load feeds NT
@@ -1331,6 +1339,44 @@ __global__ void k_stage1_sums(float* __restrict__ dx1, const float* __restrict__
     o[3] = r3;
   }
 }
+// Stage 2 of a block, adjoint side, in one pass: dbn = dy [BN(u) > 0], per
+// channel over one slice S1 = sum dbn and S2 = sum dbn (u - mean) / sqrt(var
+// + eps) (dbeta, dgamma; part[chunk][c][2]), and out = dbn, or (scale: BN
+// with running statistics) out = dbn gam / sqrt(var + eps), the BN input's
+// adjoint.
+template <int V>
+__global__ void k_stage2_sums(const float* __restrict__ dy, const float* __restrict__ u, BnP bn,
+                              float* __restrict__ out, float* __restrict__ part, int B, int C, int n, int S,
+                              int scale) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x, chunk = blockIdx.y;
+  const long e0 = (long)chunk * S, e1 = min((long)B * n, e0 + S);
+  const float is = rsqrtf(bn.v[c] + 1e-5f), m = bn.m[c], g = bn.g[c], be = bn.b[c], f = scale ? g * is : 1.f;
+  float s1 = 0.f, s2 = 0.f;
+  for (int b = (int)(e0 / n); (long)b * n < e1; ++b) {
+    const size_t base = ((size_t)b * C + c) * n;
+    const int q0 = (int)max(e0 - (long)b * n, 0L), q1 = (int)min(e1 - (long)b * n, (long)n);
+    for (int q = q0 + V * threadIdx.x; q < q1; q += V * blockDim.x) {
+      float d[V], a[V];
+      ldv<V>(dy + base + q, d);
+      ldv<V>(u + base + q, a);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const float xh = (a[e] - m) * is;
+        d[e] = g * xh + be > 0.f ? d[e] : 0.f;
+        s1 += d[e];
+        s2 += d[e] * xh;
+        d[e] *= f;
+      }
+      stv<V>(out + base + q, d);
+    }
+  }
+  const float r1 = block_sum(s1, sh), r2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    part[((size_t)chunk * C + c) * 2] = r1;
+    part[((size_t)chunk * C + c) * 2 + 1] = r2;
+  }
+}
 // part[chunk][c][4] of k_stage1_sums summed over chunks in FP64, one warp per
 // (c, k) as k_reduce_few: S0 is added to the three dbeta, Sk to dgamma_k.
 __global__ void __launch_bounds__(256) k_reduce_stage1(const float* __restrict__ part, int nchunks, int C,
@@ -1442,12 +1488,6 @@ __global__ void k_bn(const float* __restrict__ x, float* __restrict__ y, const f
 }
 
 // stage 1: x1 = ReLU(BN1(t1) + BN2(t2) + BN3(x))
-struct BnP {
-  const float *g, *b, *m, *v;
-};
-__device__ __forceinline__ float bnv(const BnP& q, int c, float x) {
-  return q.g[c] * (x - q.m[c]) * rsqrtf(q.v[c] + 1e-5f) + q.b[c];
-}
 template <int V>
 __global__ void k_stage1(const float* t1, const float* t2, const float* x, float* x1, BnP b1, BnP b2, BnP b3,
                          int planes, int C, int n) {
@@ -1629,22 +1669,6 @@ __global__ void k_eca_dy(const float* dout, const float* sc, const float* dgm, f
 #pragma unroll
     for (int e = 0; e < V; ++e) a[e] = s * a[e] + d;
     stv<V>(dy + idx, a);
-  }
-}
-// dbn = dy [BN(u) > 0]
-template <int V>
-__global__ void k_relu_bn_mask(const float* dy, const float* u, BnP bn, float* dbn, int planes, int C, int n) {
-  const int q = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-  if (q >= n) return;
-  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
-    const int c = pl % C;
-    const size_t idx = (size_t)pl * n + q;
-    float a[V], b[V];
-    ldv<V>(dy + idx, a);
-    ldv<V>(u + idx, b);
-#pragma unroll
-    for (int e = 0; e < V; ++e) a[e] = bnv(bn, c, b[e]) > 0.f ? a[e] : 0.f;
-    stv<V>(dbn + idx, a);
   }
 }
 // out (+)= a * gam / sqrt(var + eps)
@@ -2300,13 +2324,16 @@ size_t train_step_plan(const TrainArgs& a, void* arena_v) {
       k_eca_back<<<B, 64, 0, st>>>(ds, t.s, t.g, P + C.eca[b], dgm, dkp, B, co, n2);
       reduce(dkp, B, 3, 1, 0, C.eca[b]);
       plane_launch(tot2, (long)n2, k_eca_dy<4>, k_eca_dy<1>, dcur, t.s, dgm, dy, planes(tot2, n2), n2);
-      // main branch: dbn = dy [BN(u) > 0]; du = dbn gam / sigma
+      // main branch: dbn = dy [BN(u) > 0] and its dbeta, dgamma sums; du =
+      // dbn gam / sigma (scaled in the same pass with running statistics)
       BnP bn = bnp(C.g[b], C.be[b], C.m[b], C.v[b]);
-      plane_launch(tot2, (long)n2, k_relu_bn_mask<4>, k_relu_bn_mask<1>, dy, t.u, bn, dtmp, planes(tot2, n2), co,
-                   n2);
+      const Slices sl = slices((long)B * n2, co, 2L * co, 4, kSliceBlocks);
+      (n2 % 4 == 0 ? k_stage2_sums<4> : k_stage2_sums<1>)<<<dim3(co, sl.n), kT, 0, st>>>(
+          dy, t.u, bn, dtmp, part, B, co, (int)n2, sl.S, a.bn_batch ? 0 : 1);
+      k_reduce_few<<<cdiv(2L * co, 8), 256, 0, st>>>(part, sl.n, 2 * co, 1, 0, gacc, C.be[b], C.g[b], nullptr, 1.0);
     }
-    chan(dtmp, t.u, Q + C.m[b], Q + C.v[b], co, n2, C.g[b], C.be[b]);
-    bn_dx(dtmp, t.u, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), C.g[b], C.be[b], dtmp, tot2, co, n2, 0);
+    if (a.bn_batch)
+      bn_dx(dtmp, t.u, bnp(C.g[b], C.be[b], C.m[b], C.v[b]), C.g[b], C.be[b], dtmp, tot2, co, n2, 0);
     if (run) {
       cudaMemsetAsync(dx1, 0, sizeof(float) * tot, st);
       cudaMemsetAsync(dx, 0, sizeof(float) * tot, st);
