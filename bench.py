@@ -16,7 +16,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -45,8 +44,13 @@ MACS_PER_PX = sum(KERNEL_MACS_PER_PX.values())  # 5277
 # on the FP32 FMA pipe.
 KERNEL_TC_MACS_PER_PX = {"enc1_stem": 576, "enc2": 576, "enc3": 576, "dec1": 1024, "dec2": 1024, "dec3": 1024,
                          "out": 0}
-SM_COUNT, FP32_LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.070
-FFMA_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ / 1e3  # 80.5
+FP32_LANES_PER_SM = 128
+
+
+def ffma_peak_tflops(sm_count: int, sm_max_mhz: float) -> float:
+    """FP32 FMA peak from the unit counts and the clock: SMs x 128 lanes x
+    2 FLOP x maximum SM clock (152 SMs at 2070 MHz: 80.5 TFLOP/s)."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz / 1e6
 FP8_OVER_BF16 = 4.5 / 2.25  # nominal dense ratio
 
 
@@ -82,14 +86,12 @@ def whole_job_rate(world: int, per_rank: int, steps: int, max_ms: float) -> floa
 
 
 def ncu_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
-    workload (profiles/ncu_tc_<workload>.md), or None when there is none or
-    a kernel source changed since the capture (its sha256 differs)."""
-    path = os.path.join(ROOT, "profiles", f"ncu_tc_{workload}.md")
+    """DRAM bytes per launch of `kernel` from the committed ncu record of this
+    workload (profiles/traffic.json), or None when there is none or a kernel
+    source changed since the capture (its sha256 differs)."""
     try:
-        with open(path) as f:
-            m = re.search(r"<!-- traffic (\{.*?\}) -->", f.read())
-        rec = json.loads(m.group(1)) if m else None
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(workload)
         if not rec or rec.get("kernel") != kernel:
             return None
         for src, digest in rec["sources"].items():
@@ -350,7 +352,16 @@ def train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda):
     ttot, tms = time_steps(lambda: tctx.backward(tx, target=tclean))
     tctx.backward_bn(tx, target=tclean, mode="batch")
     btot, _ = time_steps(lambda: tctx.backward_bn(tx, target=tclean, mode="batch"))
-    train = {"value": whole_job_rate(world, wt.batch, args.train_steps, ttot), "unit": UNIT,
+    # algorithmic FLOPs of one step: forward, input gradients and weight
+    # gradients each cost the forward's multiply-accumulates (3 x 5277 MAC
+    # per pixel), all on the FP32 FMA pipe
+    _, mhz, ffma_peak = device_peaks(dev)
+    tflops = 2.0 * 3 * MACS_PER_PX * wt.batch * gt.P * gt.Q / (ttot / args.train_steps / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": tflops, "peak": ffma_peak, "unit": "TFLOP/s", "frac": tflops / ffma_peak,
+            "traffic": None, "flops_per_step": 2.0 * 3 * MACS_PER_PX * wt.batch * gt.P * gt.Q,
+            "peak_source": f"FP32 FMA at {mhz:.0f} MHz (derived)",
+            "note": "whole step: forward + input gradients + weight gradients = 3 x the forward MACs"}
+    train = {"value": whole_job_rate(world, wt.batch, args.train_steps, ttot), "unit": UNIT, "roofline": roof,
              "ms_per_step": ttot / args.train_steps, "p99_ms": float(np.percentile(tms, 99)),
              "workload": wt.name, "batch": wt.batch, "steps": args.train_steps,
              "step": "forward with tape + adjoint + MSE vs clean maps, FP32 arithmetic on CUDA cores, bf16 I/O",
@@ -360,6 +371,117 @@ def train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda):
                                      "step": "the same with BatchNorm in training mode (batch statistics)"}}
     del tctx
     return train
+
+
+def device_peaks(dev):
+    """(SM count of the device, maximum SM clock in MHz, FP32 FMA peak in
+    TFLOP/s derived from them)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sms, mhz, ffma_peak_tflops(sms, mhz)
+
+
+def forward_leg(stda, w, steps, warmup, ctx_env, keep=False):
+    """Times `steps` forward passes of workload w (batch resident in HBM, L2
+    flushed between steps) with CUDA events on the launching stream, with
+    per-kernel event times from the library; returns the measurement (and,
+    with keep, the context and tensors for the end-to-end leg)."""
+    import torch
+
+    rank, world, dist, dev, stream, flush, barrier, local = ctx_env
+    g = w.gen
+    B, H, W = w.batch, g.P, g.Q
+    dtype = torch.float32 if w.precision == "fp32" else torch.bfloat16
+    ctx = stda.Context(H, W, B, w.precision, 0)
+    x, _, _, _ = stda.generate(g, 0, w.cid, first_window(rank, B), B, dtype=dtype, with_clean=False)
+    out = torch.empty((B, 1, H, W), dtype=dtype, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        ctx.forward(x, out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            ctx.forward(x, out)
+            ev[i][1].record(stream)
+        barrier()
+    launches = ctx.launch_count() - launches0
+    kt = ctx.profile_read()
+    ctx.profile(False)
+    assert ctx.device_status() == stda.OK
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = reduce_max(sum(step_ms), dist, dev)
+    ms_per_step = tot_ms / steps
+    res = {"value": whole_job_rate(world, B, steps, tot_ms), "unit": UNIT, "ms_per_step": ms_per_step,
+           "steps": steps, "warmup": warmup,
+           "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+           "config": {"workload": w.name, "batch": B, "H": H, "W": W, "precision": w.precision,
+                      "accumulate": "fp32", "l2": "flushed (256 MB write) between timed steps"},
+           "gpu_launches": int(launches), "clocks": clk.summary()}
+    res.update(rooflines(w, kt, ms_per_step, dev))
+    if keep:
+        return res, (ctx, x, out, dtype)
+    del ctx, x, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def rooflines(w, kt, ms_per_step, dev):
+    """HBM fraction of the step, the dominant kernel's roofline (tensor pipe
+    and FP32 FMA pipe; the larger fraction names the bound) and the whole
+    step against the binding compute roofline."""
+    hbm_gbs, bf16_tf, _, peak_src = load_peaks()
+    sms, mhz, ffma_peak = device_peaks(dev)
+    g = w.gen
+    B, H, W = w.batch, g.P, g.Q
+    esz = 4 if w.precision == "fp32" else 2
+    px = B * H * W
+    bytes_per_step = B * 4 * H * W * esz  # 3 input maps + 1 output map per window
+    hbm_achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
+    name = max(kt, key=lambda k: kt[k][0])
+    k_ms, k_n = kt[name]
+    k_avg_s = k_ms / max(k_n, 1) / 1e3
+    tc = w.precision != "fp32"
+    tc_macs = KERNEL_TC_MACS_PER_PX[name] if tc else 0
+    fma_macs = KERNEL_MACS_PER_PX[name] - tc_macs
+    alu_tf = 2.0 * fma_macs * px / k_avg_s / 1e12
+    tc_tf = 2.0 * tc_macs * px / k_avg_s / 1e12
+    tc_peak = bf16_tf * (FP8_OVER_BF16 if w.precision.startswith("fp8") else 1.0)
+    fr_alu, fr_tc = alu_tf / ffma_peak, tc_tf / tc_peak
+    shares = {k: round(v[0] / max(sum(u[0] for u in kt.values()), 1e-12), 4) for k, v in kt.items()}
+    fma_src = f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived)"
+    if fr_tc > fr_alu:
+        bound, ach, peak, psrc = "tensor", tc_tf, tc_peak, (
+            f"{peak_src} bf16 burst {bf16_tf} TFLOP/s" + (" x 2 (fp8/bf16 nominal)" if tc_peak != bf16_tf else ""))
+    else:
+        bound, ach, peak, psrc = "alu", alu_tf, ffma_peak, fma_src
+    roofline = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": ncu_traffic(w.name, name), "peak_source": psrc,
+                "alu": {"achieved": alu_tf, "peak": ffma_peak, "frac": fr_alu, "flops_per_launch": 2.0 * fma_macs * px},
+                "tensor": {"achieved": tc_tf, "peak": tc_peak, "frac": fr_tc, "flops_per_launch": 2.0 * tc_macs * px},
+                "avg_launch_ms": k_avg_s * 1e3, "time_shares": shares}
+    tc_total = sum(KERNEL_TC_MACS_PER_PX.values()) if tc else 0
+    t_tensor_us = 2.0 * tc_total * px / (tc_peak * 1e12) * 1e6
+    t_fma_us = 2.0 * (MACS_PER_PX - tc_total) * px / (ffma_peak * 1e12) * 1e6
+    step_roofline = {"t_tensor_us": t_tensor_us, "t_fma_us": t_fma_us, "bound_us": max(t_tensor_us, t_fma_us),
+                     "measured_us": ms_per_step * 1e3, "frac": max(t_tensor_us, t_fma_us) / (ms_per_step * 1e3),
+                     "peaks": f"tensor {tc_peak:.0f} TFLOP/s, FP32 FMA {ffma_peak:.1f} TFLOP/s"}
+    return {"hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_gbs, "frac": hbm_achieved / hbm_gbs,
+                    "bytes_per_step": bytes_per_step, "peak_source": peak_src},
+            "compute": {"macs_per_px": MACS_PER_PX, "tflops": 2.0 * MACS_PER_PX * px / (ms_per_step / 1e3) / 1e12},
+            "roofline": roofline, "step_roofline": step_roofline}
 
 
 def main():
@@ -375,6 +497,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=5)
     ap.add_argument("--train-only", action="store_true", help="run only the training-step measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other forward workloads (FP32 1 x 3x64x64, FP8 1024 x 3x512x256)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -403,60 +527,28 @@ def main():
     Bld.build()
     from paper_2307_09063_gb300 import stda
 
-    if args.train_only:
-        # the training leg alone (for launch lists of the training kernels)
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-        def barrier():
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize()
-
-        train = train_leg(args, rank, world, dist, dev, torch.cuda.current_stream(), flush, barrier, stda)
-        if rank == 0:
-            print(json.dumps({"train_fwd_bwd": train}))
-        if dist:
-            dist.destroy_process_group()
-        return
-
-    g = w.gen
-    B, H, W = w.batch, g.P, g.Q
-    dtype = torch.float32 if w.precision == "fp32" else torch.bfloat16
-    esz = 4 if w.precision == "fp32" else 2
-    ctx = stda.Context(H, W, B, w.precision, 0)
-    x, _, _, _ = stda.generate(g, 0, w.cid, first_window(rank, B), B, dtype=dtype, with_clean=False)
-    out = torch.empty((B, 1, H, W), dtype=dtype, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-    torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        ctx.forward(x, out)
-    torch.cuda.synchronize()
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ctx.profile(True)
-    launches0 = ctx.launch_count()
-    with ClockSampler(local) as clk:
-        barrier()
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            ev[i][0].record(stream)
-            ctx.forward(x, out)
-            ev[i][1].record(stream)
-        barrier()
-    launches = ctx.launch_count() - launches0
-    kt = ctx.profile_read()
-    ctx.profile(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = reduce_max(sum(step_ms), dist, dev)
-    ms_per_step = tot_ms / args.steps
-    value = whole_job_rate(world, B, args.steps, tot_ms)
+    if args.train_only:
+        # the training leg alone (for launch lists of the training kernels)
+        train = train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda)
+        if rank == 0:
+            print(json.dumps({"train_fwd_bwd": train}))
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    env = (rank, world, dist, dev, stream, flush, barrier, local)
+    main_res, (ctx, x, out, dtype) = forward_leg(stda, w, args.steps, args.warmup, env, keep=True)
+    g = w.gen
+    B, H, W = w.batch, g.P, g.Q
+    esz = 4 if w.precision == "fp32" else 2
 
     # end to end through the public API on host buffers (stda_forward_host):
     # every step copies its pinned host input to the device, denoises it and
@@ -475,71 +567,39 @@ def main():
         ctx.forward_host(xh, oh)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_ms = reduce_max(e2e_ms, dist, dev)
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dist, dev)
     e2e_value = whole_job_rate(world, B, args.steps, e2e_ms)
+    del ctx, x, out
+    torch.cuda.empty_cache()
+
+    # the other forward workloads: FP32 batch 1 (3 x 64 x 64) and FP8 1024 x 3 x 512 x 256
+    configs = {}
+    if not args.no_configs:
+        for name, steps in (("fp32_b1_3x64x64", 50), ("fp8_b1024_3x512x256", 5)):
+            if name != w.name:
+                configs[name] = forward_leg(stda, workload(name), steps, 3, env)
 
     # fwd + bwd: the training step (stda_backward, MSE against the clean maps)
     # on 64 windows of 3 x 256 x 128, one step per timed iteration
     train = None
-    if not args.no_train and world >= 1:
+    if not args.no_train:
         train = train_leg(args, rank, world, dist, dev, stream, flush, barrier, stda)
 
-    hbm_gbs, bf16_tf, bf16_tf_sus, peak_src = load_peaks()
-    bytes_per_step = B * 4 * H * W * esz  # 3 input maps + 1 output map per window
-    hbm_achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
-    # dominant kernel by measured time share; its FMA-pipe and tensor-pipe
-    # fractions, the larger one naming the bound
-    name = max(kt, key=lambda k: kt[k][0])
-    k_ms, k_n = kt[name]
-    k_avg_s = k_ms / max(k_n, 1) / 1e3
-    px = B * H * W
-    tc_macs = KERNEL_TC_MACS_PER_PX[name] if w.precision != "fp32" else 0
-    fma_macs = KERNEL_MACS_PER_PX[name] - tc_macs
-    alu_tf = 2.0 * fma_macs * px / k_avg_s / 1e12
-    tc_tf = 2.0 * tc_macs * px / k_avg_s / 1e12
-    tc_peak = bf16_tf * (FP8_OVER_BF16 if w.precision.startswith("fp8") else 1.0)
-    fr_alu, fr_tc = alu_tf / FFMA_PEAK_TFLOPS, tc_tf / tc_peak
-    shares = {k: round(v[0] / max(sum(u[0] for u in kt.values()), 1e-12), 4) for k, v in kt.items()}
-    if fr_tc > fr_alu:
-        bound, ach, peak, psrc = "tensor", tc_tf, tc_peak, (
-            f"{peak_src} bf16 burst {bf16_tf} TFLOP/s" + (" x 2 (fp8/bf16 nominal)" if tc_peak != bf16_tf else ""))
-    else:
-        bound, ach, peak, psrc = "alu", alu_tf, FFMA_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
-    roofline = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": ncu_traffic(w.name, name), "peak_source": psrc,
-                "alu": {"achieved": alu_tf, "peak": FFMA_PEAK_TFLOPS, "frac": fr_alu,
-                        "flops_per_launch": 2.0 * fma_macs * px},
-                "tensor": {"achieved": tc_tf, "peak": tc_peak, "frac": fr_tc, "flops_per_launch": 2.0 * tc_macs * px},
-                "avg_launch_ms": k_avg_s * 1e3, "time_shares": shares}
-    # the whole step against the binding compute roofline: the dense convs
-    # at the tensor peak and the thin / depthwise / stem / output work at the
-    # FP32 FMA peak, which can run concurrently, so the bound is the larger
-    px_step = B * H * W
-    tc_total = sum(KERNEL_TC_MACS_PER_PX.values()) if w.precision != "fp32" else 0
-    t_tensor_us = 2.0 * tc_total * px_step / (tc_peak * 1e12) * 1e6
-    t_fma_us = 2.0 * (MACS_PER_PX - tc_total) * px_step / (FFMA_PEAK_TFLOPS * 1e12) * 1e6
-    step_roofline = {"t_tensor_us": t_tensor_us, "t_fma_us": t_fma_us, "bound_us": max(t_tensor_us, t_fma_us),
-                     "measured_us": ms_per_step * 1e3,
-                     "frac": max(t_tensor_us, t_fma_us) / (ms_per_step * 1e3),
-                     "peaks": f"tensor {tc_peak:.0f} TFLOP/s, FP32 FMA {FFMA_PEAK_TFLOPS:.1f} TFLOP/s"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3x2"}.get(w.precision, w.precision),
+    line = {"metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3x2"}.get(w.precision, w.precision),
             "data": "synthetic (seeded FMCW targets, interferers, noise; GPU generator)",
-            "config": {"workload": w.name, "batch": B, "H": H, "W": W, "precision": w.precision,
-                       "accumulate": "fp32", "l2": "flushed (256 MB write) between timed steps",
-                       "parallelism": f"replicas x{world}"},
-            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
-            "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_gbs, "frac": hbm_achieved / hbm_gbs,
-                    "bytes_per_step": bytes_per_step, "peak_source": peak_src},
-            "compute": {"macs_per_px": MACS_PER_PX, "tflops": 2.0 * MACS_PER_PX * B * H * W / (ms_per_step / 1e3) / 1e12},
-            "roofline": roofline,
-            "step_roofline": step_roofline,
+            "config": dict(main_res["config"], parallelism=f"replicas x{world}"),
+            "p50_ms": main_res["p50_ms"], "p99_ms": main_res["p99_ms"],
+            "hbm": main_res["hbm"], "compute": main_res["compute"], "roofline": main_res["roofline"],
+            "step_roofline": main_res["step_roofline"],
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * esz),
                     "d2h_bytes_per_step": int(oh.numel() * esz),
                     "call": "stda_forward_host on pinned host buffers; each step's input copy overlaps the previous step's kernels; L2 flush inside the region"},
-            "clocks": clk.summary(), "gpu_launches": int(launches)}
+            "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"]}
+    if configs:
+        line["configs"] = configs
     if train:
         line["train_fwd_bwd"] = train
     if not args.no_serving:

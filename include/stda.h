@@ -268,9 +268,21 @@ stda_status stda_serve_close(stda_ctx* ctx, int radar_id,
 size_t stda_serve_bytes(stda_ctx* ctx);
 int stda_serve_radars(stda_ctx* ctx);
 
-/* Sticky device-side error word of the context (STDA_OK or
- * STDA_ERR_TIMEOUT); synchronises the context's last stream. */
+/* Device-side error word of the context (STDA_OK or STDA_ERR_TIMEOUT):
+ * synchronises the context's last stream and every serving stream, returns
+ * the word and clears it, so a later call reports only errors raised after
+ * this one. A kernel that gives up on a bounded wait finishes the work it
+ * has queued on the tensor cores, frees its tensor memory and returns, so
+ * the context stays usable after a timeout. */
 stda_status stda_device_status(stda_ctx* ctx);
+/* Bound of the tensor-core kernels' waits for their tiles' MMAs, in polls
+ * of an mbarrier (each poll may itself suspend briefly); default 2^22, far
+ * above any tile's latency. 0 makes every such wait give up at once, so the
+ * next forward reports STDA_ERR_TIMEOUT through stda_device_status: a hook
+ * for tests of the timeout path (its output is then undefined). The waits
+ * for MMAs already issued, before tensor memory is freed, keep the default
+ * bound. */
+stda_status stda_set_wait_limit(stda_ctx* ctx, uint32_t polls);
 const char* stda_last_error(stda_ctx* ctx);
 const char* stda_status_string(stda_status s);
 
@@ -287,19 +299,23 @@ const char* stda_status_string(stda_status s);
  * passes the canonical parameters and BN buffers already in device memory
  *   d_params  [137915] float, d_buffers [1360] float (stda_init_params order)
  * and the input / output windows (d_in [B][3][H][W], d_out [B][1][H][W],
- * float). The folded weights and all activation scratch live in one
- * file-scope device array of 8 MiB that every GPU loading the library holds
- * until the process exits; it fits up to 65,536 map pixels per call (B*H*W,
- * e.g. one 256 x 256 window or sixteen 64 x 64 windows). Larger calls return
- * STDA_ERR_SHAPE without launching anything.
+ * float). The folded weights (BN folded in FP32 on the GPU at every call)
+ * and all activation scratch live in one file-scope device array of 8 MiB
+ * that every GPU loading the library holds until the process exits. A call
+ * takes at most 65,536 map pixels (B*H*W; e.g. one 256 x 256 window or
+ * sixteen 64 x 64 windows); larger calls return STDA_ERR_SHAPE without
+ * launching anything.
  *
  * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture. Every call on a device shares the one array and overwrites it:
- * calls whose work overlaps on the GPU (different streams, or different
- * host threads without ordering) race and corrupt each other's results.
- * Nothing in the array needs to start at zero: each call writes every value
- * it later reads. */
+ * device (cudaGetSymbolAddress). With CUDA's lazy module loading that first
+ * call (or the library's first kernel launch on the device) is also when
+ * the module is loaded and the 8 MiB are placed in device memory, so a
+ * caller that cannot allocate later should make one call at start-up, and
+ * before any stream capture. Every call on a device shares the one array
+ * and overwrites it: calls whose work overlaps on the GPU (different
+ * streams, or different host threads without ordering) race and corrupt
+ * each other's results. Nothing in the array needs to start at zero: each
+ * call writes every value it later reads. */
 stda_status stda_forward_static(const float* d_params, const float* d_buffers,
                                 const float* d_in, float* d_out, int B, int H,
                                 int W, struct CUstream_st* stream);

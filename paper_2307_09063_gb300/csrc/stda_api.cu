@@ -407,7 +407,6 @@ struct stda_ctx {
   size_t d_tc_bytes = 0;
   stda::TcPackOffsets tc_off;
   stda::TcWeights tcw;
-  bool force_simt = false;  // STDA_FORCE_SIMT=1: BF16 on the CUDA-core kernels
   float* d_canon = nullptr;  // canonical parameters + BN buffers (training graph)
   void* d_train = nullptr;   // training workspace
   size_t train_bytes = 0;
@@ -416,6 +415,7 @@ struct stda_ctx {
   void* d_scratch = nullptr;
   size_t scratch_size = 0;
   int* d_status = nullptr;
+  uint32_t wait_polls = stda::kWaitPolls;  // bound of the tensor-core kernels' tile waits
   cudaStream_t last_stream = nullptr;
   // host-buffer forward: two staging pairs (max_batch windows each), copy
   // streams, and per pair the events input copied / forward done / output copied
@@ -514,8 +514,6 @@ stda_status stda_create(const stda_config* cfg, stda_ctx** out) {
   c->cfg = *cfg;
   c->frames = frames;
   cudaGetDevice(&c->device);
-  const char* fs = getenv("STDA_FORCE_SIMT");
-  c->force_simt = fs && fs[0] == '1';
   c->params.resize(stda::num_params(frames));
   c->buffers.resize(stda::kNumBuffers);
   stda::init_params(cfg->weight_seed, c->params.data(), c->buffers.data(), frames);
@@ -643,13 +641,10 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
     case STDA_BF16:
     case STDA_FP8_E4M3:
     case STDA_FP8_E4M3_FAST:
-      if (c->force_simt || c->cfg.prec == STDA_FP32) {
-        e = stda::forward_simt<__nv_bfloat16>(c->net, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H,
-                                              W, s, st, &c->prof);
-      } else {
+      {
         int tiles[6];
         e = stda::forward_tc(c->net, c->tcw, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W, s,
-                             c->d_status, st, &c->prof, tiles);
+                             c->d_status, st, &c->prof, tiles, c->wait_polls);
         if (!e)
           e = stda::launch_out_bf16(c->net, (const __nv_bfloat16*)s.act[5], s.part[5], tiles[5],
                                     (__nv_bfloat16*)d_out, B, H, W, st, &c->prof);
@@ -814,10 +809,18 @@ stda_status stda_device_status(stda_ctx* c) {
   if (!c) return STDA_ERR_INVALID_ARG;
   int h = 0;
   cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (!e && c->serve) e = stda::serve_sync(c->serve);
   if (e) return cuda_fail(c, e, "device_status");
   e = cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (!e && h != STDA_OK) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e) return cuda_fail(c, e, "device_status");
   return (stda_status)h;
+}
+
+stda_status stda_set_wait_limit(stda_ctx* c, uint32_t polls) {
+  if (!c) return STDA_ERR_INVALID_ARG;
+  c->wait_polls = polls;
+  return STDA_OK;
 }
 
 const char* stda_last_error(stda_ctx* c) { return c ? c->err.c_str() : "null context"; }

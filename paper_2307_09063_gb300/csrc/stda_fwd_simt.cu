@@ -22,13 +22,10 @@ namespace stda {
 namespace {
 
 __device__ __forceinline__ float tof(float v) { return v; }
-__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename T>
 __device__ __forceinline__ T fromf(float v);
 template <>
 __device__ __forceinline__ float fromf<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 fromf<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
 constexpr int kThreads = 256;
 
@@ -653,7 +650,5 @@ cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float*
 
 template cudaError_t forward_simt<float>(const NetW&, const float*, float*, int, int, int, const FwdScratch&,
                                          cudaStream_t, KernelHook*);
-template cudaError_t forward_simt<__nv_bfloat16>(const NetW&, const __nv_bfloat16*, __nv_bfloat16*, int, int,
-                                                 int, const FwdScratch&, cudaStream_t, KernelHook*);
 
 }  // namespace stda

@@ -260,15 +260,16 @@ __device__ void fill_desc_table(uint2* tab, const KStep* ks, int nsteps, int nph
   }
 }
 
-// Issues the MMAs of one tile: 2 * nph accumulators (main then residual per
-// output phase) of nsteps K-steps each, from the descriptor table. dm is the
-// tile's A shift from the first tile, in 16-byte units (one pixel).
+// Issues the MMAs of one tile: nacc accumulators (main then residual per
+// output phase; one for the stem) of nsteps K-steps each, from the
+// descriptor table, accumulator a at TMEM column a * NP. dm is the tile's A
+// shift from the first tile, in 16-byte units (one pixel).
 template <bool F8>
-__device__ __forceinline__ void issue_tile(uint32_t d_base, const uint2* tab, int nsteps, int nph, int NP,
+__device__ __forceinline__ void issue_tile(uint32_t d_base, const uint2* tab, int nsteps, int nacc, int NP,
                                            uint32_t dm, int terms, uint32_t a_lo, uint32_t b_lo) {
   const uint32_t idesc = F8 ? idesc_e4m3(128, NP) : idesc_bf16(128, NP);
   const uint64_t hi = (uint64_t)kDescHi << 32;
-  for (int acc = 0; acc < 2 * nph; ++acc) {
+  for (int acc = 0; acc < nacc; ++acc) {
     const uint2* t = tab + acc * nsteps;
     const uint32_t d = d_base + (uint32_t)(acc * NP);
 #pragma unroll 4
@@ -429,22 +430,24 @@ __device__ __forceinline__ float epi(float m, float r, float sm, float sr, float
   return fmaxf(m * sm + b2, 0.f) + r * sr + rb;
 }
 
-// The tiles of one item. TMEM buffer b (< a.nbuf) has a.gpb warp groups
-// (1 or 2; group g serves buffer g / gpb as part g % gpb), slots
+// The `ntile` tiles of one item. TMEM buffer b (< a.nbuf) has a.gpb warp
+// groups (1 or 2; group g serves buffer g / gpb as part g % gpb), slots
 // (b * nslot + s) * cpt, s < nslot, mbarriers 2 b + s and the tiles b,
 // b + nbuf, ...: the first thread of its part-0 group issues a tile's MMAs
+// (nacc accumulators of nsteps K-steps from descriptor table `tab`, N = NM)
 // and commits them, its groups drain the accumulators (warp 4 g + q reads
 // TMEM lanes 32 q .. 32 q + 31; with two groups each drains its part of the
 // columns) through drain(tile, column, part, parts). With two slots the next
 // tile is queued before the drain, so the tensor core runs it meanwhile;
 // buffers run unsynchronised, so one buffer's drain also overlaps other
 // buffers' MMAs. Bounded waits; a timeout is agreed per buffer (the issuer
-// gives its queued MMAs a second bounded wait) and returned as false.
-// `phases` holds bit 2 b + s = parity of that barrier's next completion.
+// gives its queued MMAs a second wait with the default bound) and returned
+// as false. `phases` holds bit 2 b + s = parity of that barrier's next
+// completion.
 template <bool F8, typename Drain>
 __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32_t tmem, uint32_t& phases,
-                                          int cpt, int nsteps, int nph, int NM, int T, uint32_t a_lo,
-                                          uint32_t b_lo, Drain drain) {
+                                          int cpt, const uint2* tab, int ntile, int nsteps, int nacc, int NM,
+                                          int T, uint32_t a_lo, uint32_t b_lo, Drain drain) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gpb = a.gpb;
   const int bi = (warp >> 2) / gpb, part = (warp >> 2) % gpb, nb = a.nbuf, ns = a.nslot;
   bool ok = true;
@@ -453,18 +456,18 @@ __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32
     uint32_t par = (phases >> (2 * bi)) & 3u;
     auto issue = [&](int tile, int s) {
       fence_after_sync();
-      issue_tile<F8>(tmem + (uint32_t)((bi * ns + s) * cpt), M.dtab, nsteps, nph, NM, (uint32_t)(128 * tile), T,
+      issue_tile<F8>(tmem + (uint32_t)((bi * ns + s) * cpt), tab, nsteps, nacc, NM, (uint32_t)(128 * tile), T,
                      a_lo, b_lo);
       commit(M.bar + 2 * bi + s);
     };
-    if (issuer && bi < a.ntile) issue(bi, 0);
+    if (issuer && bi < ntile) issue(bi, 0);
     int k = 0;
-    for (int i = bi; i < a.ntile; i += nb, ++k) {
+    for (int i = bi; i < ntile; i += nb, ++k) {
       const int s = ns == 2 ? (k & 1) : 0;
-      const bool next = i + nb < a.ntile;
+      const bool next = i + nb < ntile;
       if (ns == 2 && issuer && next) issue(i + nb, s ^ 1);
       __syncwarp();
-      ok = mbar_wait(M.bar + 2 * bi + s, (par >> s) & 1u);
+      ok = mbar_wait(M.bar + 2 * bi + s, (par >> s) & 1u, a.wait_polls);
       par ^= 1u << s;
       fence_after_sync();
       if (ok) drain(i, (uint32_t)((bi * ns + s) * cpt), part, gpb);
@@ -483,7 +486,7 @@ __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32
   }
   // every thread advances every barrier's phase by the commits of this item
   for (int bb = 0; bb < nb; ++bb) {
-    const int n = bb < a.ntile ? (a.ntile - 1 - bb) / nb + 1 : 0;
+    const int n = bb < ntile ? (ntile - 1 - bb) / nb + 1 : 0;
     const int n0 = ns == 2 ? (n + 1) / 2 : n, n1 = ns == 2 ? n / 2 : 0;
     phases ^= ((uint32_t)(n0 & 1) << (2 * bb)) | ((uint32_t)(n1 & 1) << (2 * bb + 1));
   }
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   // 3. stage 2 on the tensor cores, 128-row tiles; 4. epilogue
   const int cpt = 2 * NP;  // TMEM columns per tile
   const bool ok = run_tiles<F8>(
-      a, M, tmem, phases, cpt, nsteps, 1, NP, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
+      a, M, tmem, phases, cpt, M.dtab, a.ntile, nsteps, 2, NP, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
       [&](int i, uint32_t col, int, int) {  // encoders drain a tile with one group
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
         int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   // stage 2 on the tensor cores and the epilogue, as in the encoder
   const int cpt = 2 * NPH * NM;  // TMEM columns per tile: (main, residual) x 4 phases
   const bool ok = run_tiles<F8>(
-      a, M, tmem, phases, cpt, nsteps, NPH, NM, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
+      a, M, tmem, phases, cpt, M.dtab, a.ntile, nsteps, 2 * NPH, NM, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
       [&](int i, uint32_t col, int part, int parts) {  // part p of `parts` drains phases 4p/parts ..
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
         int lr = m / WP, lc = m % WP, r = a0 + lr - 2, c = lc - 2;
@@ -981,16 +984,6 @@ struct Geo {
   uint32_t cols;
 };
 
-// Tuning override: STDA_TC_SLOTS=1 keeps one TMEM slot per warp group.
-int max_slots() {
-  static int m = -1;
-  if (m < 0) {
-    const char* e = getenv("STDA_TC_SLOTS");
-    m = (e && atoi(e) == 1) ? 1 : 2;
-  }
-  return m;
-}
-
 // TMEM buffers: one per warp group where the column budget allows, then a
 // second slot per buffer if every group can have one. With split = true
 // (decoders) and half as many buffers as groups, two groups share each
@@ -1005,33 +998,9 @@ void pick_buffers(Geo& g, int cpt, int budget, bool split = false) {
       g.nbuf = k;
       break;
     }
-  if (max_slots() == 2 && g.nbuf == groups && (int)pow2_cols(2 * groups * cpt) <= budget) g.nslot = 2;
+  if (g.nbuf == groups && (int)pow2_cols(2 * groups * cpt) <= budget) g.nslot = 2;
   if (split && g.nbuf && 2 * g.nbuf == groups && g.nbuf <= 2) g.gpb = 2;
   g.cols = pow2_cols(std::max(g.nbuf, 1) * g.nslot * cpt);
-}
-
-// Tuning override: STDA_TC_BANDS="e1,e2,e3,d1,d2,d3" sets each level's band
-// height (1 .. 16 rows; 0 = automatic) where that band fits.
-int band_override(int b) {
-  static int v[6] = {-1, -1, -1, -1, -1, -1};
-  if (v[0] < 0) {
-    for (int& c : v) c = 0;
-    if (const char* e = getenv("STDA_TC_BANDS")) sscanf(e, "%d,%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]);
-    for (int& c : v) c = (c >= 1 && c <= 16) ? c : 0;
-  }
-  return v[b];
-}
-
-// Geometry policy: 0 = the largest band first (default; the faster one
-// measured on 256 windows of 3 x 256 x 128 in bf16 and 1024 windows of
-// 3 x 512 x 256 in FP8); 1 = two CTAs per SM first, then the largest band. STDA_TC_POLICY overrides.
-int geo_policy() {
-  static int p = -1;
-  if (p < 0) {
-    const char* e = getenv("STDA_TC_POLICY");
-    p = e ? atoi(e) : 0;
-  }
-  return p;
 }
 
 // Plane stride skew in 16-byte pixels. In the staging and stage-1 loops one
@@ -1082,20 +1051,14 @@ Geo decoder_geo_at(int b, bool f8, int terms, int w, int TA, int pass) {
   return g;
 }
 
+// The largest band first (16, 8, 4, 2, 1 rows), and at equal band two
+// 256-thread CTAs per SM before one 512-thread CTA (measured faster on 256
+// windows of 3 x 256 x 128 in bf16 and 1024 windows of 3 x 512 x 256 in FP8
+// than preferring two CTAs per SM at a smaller band).
 Geo level_geo(int b, bool f8, int terms, int h, int w, int frames) {
-  auto at = [&](int TA, int pass) {
-    return kBlkEnc[b] ? encoder_geo_at(b, f8, terms, w, TA, pass, frames)
-                      : decoder_geo_at(b, f8, terms, w, TA, pass);
-  };
-  if (const int TA = band_override(b)) {
-    for (int pass = 0; pass < 2; ++pass) {
-      Geo g = at(TA, pass);
-      if (g.band) return g;
-    }
-  }
   for (int it = 0; it < 10; ++it) {
-    const int pass = geo_policy() ? it / 5 : it % 2, TA = 16 >> (geo_policy() ? it % 5 : it / 2);
-    Geo g = at(TA, pass);
+    const int pass = it % 2, TA = 16 >> (it / 2);
+    Geo g = kBlkEnc[b] ? encoder_geo_at(b, f8, terms, w, TA, pass, frames) : decoder_geo_at(b, f8, terms, w, TA, pass);
     if (g.band) return g;
   }
   return Geo{};
@@ -1304,7 +1267,7 @@ TcWeights tc_weights_from(const unsigned char* base, const TcPackOffsets& po) {
 
 cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* in, __nv_bfloat16* out, int B,
                        int H, int W, const FwdScratch& s, int* status, cudaStream_t st, KernelHook* hook,
-                       int* tiles_out) {
+                       int* tiles_out, uint32_t wait_polls) {
   cudaError_t e = cudaSuccess;
   int tiles[6];
   const void* prev = nullptr;
@@ -1350,6 +1313,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.out = (__nv_bfloat16*)s.act[l];
     a.part = s.part[l];
     a.status = status;
+    a.wait_polls = wait_polls;
     const int rows = kBlkEnc[l] ? h / 2 : h;
     a.tiles_per_window = cdiv(rows, g.band);
     a.nwin = B;

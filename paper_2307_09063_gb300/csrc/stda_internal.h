@@ -78,8 +78,8 @@ struct KernelHook {
   virtual ~KernelHook() {}
 };
 
-// Forward pass on the CUDA cores (FP32 arithmetic; storage T = float or
-// bfloat16). Returns cudaSuccess or the launch error.
+// Forward pass on the CUDA cores (FP32 arithmetic and storage; T = float,
+// the STDA_FP32 path). Returns cudaSuccess or the launch error.
 template <typename T>
 cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H,
                          int W, const FwdScratch& s, cudaStream_t st,

@@ -293,6 +293,12 @@ stda_status serve_close(Serve* sv, const NetW& w, const TcWeights& tw, int radar
 }
 
 size_t serve_used(const Serve* sv) { return sv->used; }
+
+cudaError_t serve_sync(Serve* sv) {
+  for (auto& kv : sv->classes)
+    if (cudaError_t e = cudaStreamSynchronize(kv.second->stream)) return e;
+  return cudaSuccess;
+}
 int serve_radars(const Serve* sv) { return (int)sv->radars.size(); }
 
 }  // namespace stda

@@ -16,6 +16,8 @@ cudaError_t serve_flush(Serve* sv, const NetW& w, const TcWeights& tw, cudaStrea
 stda_status serve_close(Serve* sv, const NetW& w, const TcWeights& tw, int radar, cudaStream_t st,
                         cudaError_t* err);
 size_t serve_used(const Serve* sv);
+// Waits for every batch in flight on the size classes' streams.
+cudaError_t serve_sync(Serve* sv);
 int serve_radars(const Serve* sv);
 
 }  // namespace stda

@@ -22,6 +22,7 @@ namespace stda {
 namespace {
 
 constexpr size_t kStaticBytes = (size_t)8 << 20;  // 8 MiB
+constexpr size_t kStaticMaxPixels = 65536;          // B * H * W per call
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
@@ -75,40 +76,42 @@ CanonOffsets canon_offsets() {
   return o;
 }
 
-// BN in inference form as an affine map: scale and shift of channel c.
-__device__ double bn_scale(const float* P, const float* Bf, int g, int v, int c) {
-  return (double)P[g + c] / sqrt((double)Bf[v + c] + 1e-5);
+// BN in inference form as an affine map: scale and shift of channel c
+// (FP32, like the forward it feeds).
+__device__ float bn_scale(const float* P, const float* Bf, int g, int v, int c) {
+  return P[g + c] / sqrtf(Bf[v + c] + 1e-5f);
 }
-__device__ double bn_shift(const float* P, const float* Bf, int g, int be, int m, int v, int c) {
-  return (double)P[be + c] - (double)Bf[m + c] * bn_scale(P, Bf, g, v, c);
+__device__ float bn_shift(const float* P, const float* Bf, int g, int be, int m, int v, int c) {
+  return P[be + c] - Bf[m + c] * bn_scale(P, Bf, g, v, c);
 }
 
 // Folds the canonical parameters into the kernels' layout (the same layout
-// and the same folding as the host path of stda_set_params), grid-stride.
+// and the same algebra as the host path of stda_set_params, which folds in
+// FP64), in FP32, grid-stride.
 __global__ void k_fold(const float* __restrict__ P, const float* __restrict__ Bf, float* __restrict__ F,
                        CanonOffsets co, FoldedOffsets fo) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
   for (int i = t0; i < 216; i += nt) {
     int o = i / 27, r = i % 27;
-    F[fo.stem_w + r * 8 + o] = (float)(P[co.stem_w + i] * bn_scale(P, Bf, co.stem_g, co.stem_v, o));
+    F[fo.stem_w + r * 8 + o] = P[co.stem_w + i] * bn_scale(P, Bf, co.stem_g, co.stem_v, o);
   }
   for (int i = t0; i < 8; i += nt)
-    F[fo.stem_b + i] = (float)bn_shift(P, Bf, co.stem_g, co.stem_b, co.stem_m, co.stem_v, i);
+    F[fo.stem_b + i] = bn_shift(P, Bf, co.stem_g, co.stem_b, co.stem_m, co.stem_v, i);
   const int cins[6] = {8, 16, 32, 64, 32, 16}, couts[6] = {16, 32, 64, 32, 16, 8};
   for (int b = 0; b < 6; ++b) {
     const int ci = cins[b], cout = couts[b];
     const bool enc = b < 3;
     for (int i = t0; i < 9 * ci; i += nt) {
       int t = i / ci, ch = i % ci;
-      double k = bn_scale(P, Bf, co.g2[b], co.v2[b], ch) * P[co.w3[b] + ch * 9 + (enc ? t : 8 - t)];
+      float k = bn_scale(P, Bf, co.g2[b], co.v2[b], ch) * P[co.w3[b] + ch * 9 + (enc ? t : 8 - t)];
       if (t == 4)
         k += bn_scale(P, Bf, co.g1[b], co.v1[b], ch) * P[co.w1[b] + ch] + bn_scale(P, Bf, co.g3[b], co.v3[b], ch);
-      F[fo.dw[b] + i] = (float)k;
+      F[fo.dw[b] + i] = k;
     }
     for (int ch = t0; ch < ci; ch += nt)
-      F[fo.dwb[b] + ch] = (float)(bn_shift(P, Bf, co.g1[b], co.b1[b], co.m1[b], co.v1[b], ch) +
-                                  bn_shift(P, Bf, co.g2[b], co.b2[b], co.m2[b], co.v2[b], ch) +
-                                  bn_shift(P, Bf, co.g3[b], co.b3[b], co.m3[b], co.v3[b], ch));
+      F[fo.dwb[b] + ch] = bn_shift(P, Bf, co.g1[b], co.b1[b], co.m1[b], co.v1[b], ch) +
+                          bn_shift(P, Bf, co.g2[b], co.b2[b], co.m2[b], co.v2[b], ch) +
+                          bn_shift(P, Bf, co.g3[b], co.b3[b], co.m3[b], co.v3[b], ch);
     const int dense = (enc ? 9 : 16) * ci * cout;
     for (int d = t0; d < dense; d += nt) {
       int o = d % cout, i = (d / cout) % ci, kk = d / (cout * ci);  // kk = tap, or phase * 4 + sub-tap
@@ -120,11 +123,11 @@ __global__ void k_fold(const float* __restrict__ P, const float* __restrict__ Bf
         int ky = py + 1 - 2 * (sy - 1 + py), kx = px + 1 - 2 * (sx - 1 + px);
         s = (((size_t)i * cout + o) * 4 + ky) * 4 + kx;
       }
-      F[fo.w2[b] + d] = (float)(P[co.w2[b] + s] * bn_scale(P, Bf, co.g[b], co.v[b], o));
+      F[fo.w2[b] + d] = P[co.w2[b] + s] * bn_scale(P, Bf, co.g[b], co.v[b], o);
       F[fo.rw[b] + d] = P[co.rw[b] + s];
     }
     for (int o = t0; o < cout; o += nt) {
-      F[fo.b2[b] + o] = (float)bn_shift(P, Bf, co.g[b], co.be[b], co.m[b], co.v[b], o);
+      F[fo.b2[b] + o] = bn_shift(P, Bf, co.g[b], co.be[b], co.m[b], co.v[b], o);
       F[fo.rb[b] + o] = P[co.rb[b] + o];
     }
     for (int j = t0; j < 3; j += nt) F[fo.eca[b] + j] = P[co.eca[b] + j];
@@ -168,6 +171,7 @@ extern "C" stda_status stda_forward_static(const float* d_params, const float* d
   if (B < 0 || H <= 0 || W <= 0 || H % 8 || W % 8) return STDA_ERR_SHAPE;
   if (B == 0) return STDA_OK;
   if (!d_params || !d_buffers || !d_in || !d_out) return STDA_ERR_INVALID_ARG;
+  if ((size_t)B * H * W > kStaticMaxPixels) return STDA_ERR_SHAPE;
   const FoldedOffsets fo = folded_layout();
   const size_t wbytes = (fo.total * sizeof(float) + 255) / 256 * 256;
   if (wbytes + scratch_bytes(B, H, W, sizeof(float)) > kStaticBytes) return STDA_ERR_SHAPE;

@@ -61,6 +61,7 @@ struct TcArgs {
   __nv_bfloat16* out;
   float* part;
   int* status;
+  uint32_t wait_polls;  // polls of the tile barrier before a drain wait gives up
 };
 
 // Host: packs the folded FP32 weights of every block for the tensor cores.
@@ -78,11 +79,19 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
              std::vector<unsigned char>* blob, TcPackOffsets* po);
 TcWeights tc_weights_from(const unsigned char* dev_base, const TcPackOffsets& po);
 
+// Default bound of the device-side waits for a tile's MMAs (mbarrier polls,
+// each of which may itself suspend briefly): far above any tile's latency.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 // Forward of the six blocks on the tensor cores (output conv excluded);
 // tiles_out receives the ECA partial-sum tiles per window of each block.
+// wait_polls bounds the epilogue's wait for each tile (0: give up at once,
+// which only tests of the timeout path use); on a timeout the kernel still
+// waits, with the default bound, for the MMAs it issued before it frees its
+// tensor memory, and sets *status to STDA_ERR_TIMEOUT.
 cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* in, __nv_bfloat16* out, int B,
                        int H, int W, const FwdScratch& s, int* status, cudaStream_t st, KernelHook* hook,
-                       int* tiles_out);
+                       int* tiles_out, uint32_t wait_polls = kWaitPolls);
 
 // Output conv (CUDA cores) over the decoder-3 map, bf16 I/O.
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,

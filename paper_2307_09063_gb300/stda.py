@@ -69,6 +69,7 @@ def lib():
         L.stda_forward.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_forward_host.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]
         L.stda_device_status.argtypes = [_VP]
+        L.stda_set_wait_limit.argtypes = [_VP, ctypes.c_uint32]
         L.stda_last_error.restype = ctypes.c_char_p
         L.stda_last_error.argtypes = [_VP]
         L.stda_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
@@ -323,7 +324,13 @@ class Context:
         return int(lib().stda_launch_count(self.h))
 
     def device_status(self):
+        """The device-side error word (OK or ERR_TIMEOUT), cleared by the read."""
         return lib().stda_device_status(self.h)
+
+    def set_wait_limit(self, polls=1 << 22):
+        """Bound of the tensor-core kernels' tile waits (0: give up at once,
+        for tests of the timeout path)."""
+        self._check(lib().stda_set_wait_limit(self.h, polls))
 
 
 def forward_static(d_params, d_buffers, x, out=None, stream=None):
@@ -331,7 +338,14 @@ def forward_static(d_params, d_buffers, x, out=None, stream=None):
     allocation (for callers that cannot allocate); all tensors on the GPU."""
     import torch
 
-    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.dim() == 4
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.dim() == 4 and x.shape[1] == 3
+    for t, n in ((d_params, num_params()), (d_buffers, num_buffers())):
+        # the library reads exactly n floats from each: anything else is an
+        # out-of-bounds device read, so refuse it here
+        if not (t.is_cuda and t.device == x.device and t.dtype == torch.float32 and t.is_contiguous()
+                and t.numel() == n):
+            raise StdaError(ERR_INVALID_ARG, f"forward_static: parameters must be {n} contiguous float32 "
+                                             f"values on {x.device}")
     B, _, H, W = x.shape
     if out is None:
         out = torch.empty((B, 1, H, W), dtype=torch.float32, device=x.device)
