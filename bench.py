@@ -407,7 +407,6 @@ def forward_leg(stda, w, steps, warmup, ctx_env, keep=False):
         ctx.forward(x, out)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    ctx.profile(True)
     launches0 = ctx.launch_count()
     with ClockSampler(local) as clk:
         barrier()
@@ -418,9 +417,15 @@ def forward_leg(stda, w, steps, warmup, ctx_env, keep=False):
             ev[i][1].record(stream)
         barrier()
     launches = ctx.launch_count() - launches0
+    assert ctx.device_status() == stda.OK
+    # per-kernel times in a second pass of the same steps (the library's
+    # event pairs around every launch stay out of the timed region above)
+    ctx.profile(True)
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ctx.forward(x, out)
     kt = ctx.profile_read()
     ctx.profile(False)
-    assert ctx.device_status() == stda.OK
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = reduce_max(sum(step_ms), dist, dev)
     ms_per_step = tot_ms / steps
@@ -557,7 +562,8 @@ def main():
     # launching stream around all of them, every copy inside it)
     xh = x.cpu().pin_memory()
     oh = torch.empty((B, 1, H, W), dtype=dtype).pin_memory()
-    ctx.forward_host(xh, oh)  # allocates the staging buffers
+    for _ in range(2):  # allocates the two staging pairs (and captures each one's forward)
+        ctx.forward_host(xh, oh)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()

@@ -417,6 +417,17 @@ struct stda_ctx {
   int* d_status = nullptr;
   uint32_t wait_polls = stda::kWaitPolls;  // bound of the tensor-core kernels' tile waits
   cudaStream_t last_stream = nullptr;
+  // forward passes captured as CUDA graphs, by (input, output, B, H, W), most
+  // recent last; replayed on the caller's stream (one launch instead of seven)
+  struct Graph {
+    const void* in;
+    void* out;
+    int B, H, W;
+    int launches;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;  // private stream the captures run on
   // host-buffer forward: two staging pairs (max_batch windows each), copy
   // streams, and per pair the events input copied / forward done / output copied
   void* d_hin[2] = {};
@@ -443,7 +454,15 @@ stda_status cuda_fail(stda_ctx* c, cudaError_t e, const char* where) {
 
 size_t elem_size(stda_precision p) { return p == STDA_FP32 ? 4 : 2; }
 
+// Captured forwards hold the weight, scratch and status pointers and the
+// wait bound as kernel parameters: drop them whenever one of those changes.
+void drop_graphs(stda_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
 stda_status upload_weights(stda_ctx* c) {
+  drop_graphs(c);
   std::vector<float> host(stda::folded_layout(c->frames).total);
   stda::fold_params(c->params.data(), c->buffers.data(), host.data(), &c->off, c->frames);
   cudaError_t e = cudaMemcpy(c->d_folded, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -454,7 +473,7 @@ stda_status upload_weights(stda_ctx* c) {
   bool f8[6];
   const bool fp8 = c->cfg.prec == STDA_FP8_E4M3 || c->cfg.prec == STDA_FP8_E4M3_FAST;
   for (int b = 0; b < 6; ++b) f8[b] = fp8 && b > 0;
-  stda::pack_tc(host.data(), c->off, f8, c->cfg.prec == STDA_FP8_E4M3_FAST ? 1 : 2, &blob, &c->tc_off);
+  stda::pack_tc(host.data(), c->off, c->frames, f8, c->cfg.prec == STDA_FP8_E4M3_FAST ? 1 : 2, &blob, &c->tc_off);
   if (c->d_tc && blob.size() > c->d_tc_bytes) {
     cudaFree(c->d_tc);
     c->d_tc = nullptr;
@@ -479,9 +498,36 @@ stda_status upload_weights(stda_ctx* c) {
 
 bool shape_ok(int H, int W) { return H > 0 && W > 0 && H % 8 == 0 && W % 8 == 0; }
 
+// The forward pass's kernels on `st` (seven launches; per-kernel hooks).
+cudaError_t run_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int H, int W, cudaStream_t st,
+                        stda::KernelHook* hook) {
+  const size_t es = elem_size(c->cfg.prec);
+  stda::FwdScratch s;
+  stda::scratch_carve(c->d_scratch, B, H, W, es, &s);
+  cudaError_t e;
+  if (c->cfg.prec == STDA_FP32)
+    return stda::forward_simt<float>(c->net, (const float*)d_in, (float*)d_out, B, H, W, s, st, hook);
+  int tiles[6];
+  e = stda::forward_tc(c->net, c->tcw, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W, s, c->d_status,
+                       st, hook, tiles, c->wait_polls);
+  if (!e)
+    e = stda::launch_out_bf16(c->net, (const __nv_bfloat16*)s.act[5], s.part[5], tiles[5], (__nv_bfloat16*)d_out, B,
+                              H, W, st, hook);
+  return e;
+}
+
+// Counts the launches of a captured forward.
+struct Counter : stda::KernelHook {
+  int n = 0;
+  void begin(int, cudaStream_t) override { ++n; }
+  void end(cudaStream_t) override {}
+};
+constexpr size_t kMaxGraphs = 8;
+
 }  // namespace
 
 extern "C" {
+
 
 const char* stda_status_string(stda_status s) {
   switch (s) {
@@ -562,6 +608,8 @@ stda_status stda_destroy(stda_ctx* c) {
   }
   if (c->h2d) cudaStreamDestroy(c->h2d);
   if (c->d2h) cudaStreamDestroy(c->d2h);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return STDA_OK;
 }
@@ -630,30 +678,46 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
   size_t es = elem_size(c->cfg.prec);
   if (stda::scratch_bytes(B, H, W, es) > c->scratch_size)
     return fail(c, STDA_ERR_SHAPE, "forward: B*H*W exceeds the context's scratch");
-  stda::FwdScratch s;
-  stda::scratch_carve(c->d_scratch, B, H, W, es, &s);
   c->last_stream = st;
   cudaError_t e;
-  switch (c->cfg.prec) {
-    case STDA_FP32:
-      e = stda::forward_simt<float>(c->net, (const float*)d_in, (float*)d_out, B, H, W, s, st, &c->prof);
-      break;
-    case STDA_BF16:
-    case STDA_FP8_E4M3:
-    case STDA_FP8_E4M3_FAST:
-      {
-        int tiles[6];
-        e = stda::forward_tc(c->net, c->tcw, (const __nv_bfloat16*)d_in, (__nv_bfloat16*)d_out, B, H, W, s,
-                             c->d_status, st, &c->prof, tiles, c->wait_polls);
-        if (!e)
-          e = stda::launch_out_bf16(c->net, (const __nv_bfloat16*)s.act[5], s.part[5], tiles[5],
-                                    (__nv_bfloat16*)d_out, B, H, W, st, &c->prof);
-      }
-      break;
-    default:
-      return fail(c, STDA_ERR_UNSUPPORTED, "forward: unknown precision");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (c->prof.on || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    // per-kernel timing, or the caller is capturing the stream: launch directly
+    cudaGetLastError();
+    e = run_forward(c, d_in, d_out, B, H, W, st, &c->prof);
+    if (e) return cuda_fail(c, e, "forward");
+    return STDA_OK;
   }
-  if (e) return cuda_fail(c, e, "forward");
+  size_t gi = 0;
+  while (gi < c->graphs.size()) {
+    const auto& g = c->graphs[gi];
+    if (g.in == d_in && g.out == d_out && g.B == B && g.H == H && g.W == W) break;
+    ++gi;
+  }
+  if (gi == c->graphs.size()) {
+    if (!c->cap && (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking))) return cuda_fail(c, e, "forward");
+    Counter cnt;
+    if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal))) return cuda_fail(c, e, "forward");
+    const cudaError_t fe = run_forward(c, d_in, d_out, B, H, W, c->cap, &cnt);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (fe || e) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(c, fe ? fe : e, "forward (capture)");
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) return cuda_fail(c, e, "forward (instantiate)");
+    if (c->graphs.size() == kMaxGraphs) {
+      cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({d_in, d_out, B, H, W, cnt.n, exec});
+    gi = c->graphs.size() - 1;
+  }
+  if ((e = cudaGraphLaunch(c->graphs[gi].exec, st))) return cuda_fail(c, e, "forward (graph launch)");
+  c->prof.launches += (uint64_t)c->graphs[gi].launches;
   return STDA_OK;
 }
 
@@ -819,6 +883,8 @@ stda_status stda_device_status(stda_ctx* c) {
 
 stda_status stda_set_wait_limit(stda_ctx* c, uint32_t polls) {
   if (!c) return STDA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  drop_graphs(c);
   c->wait_polls = polls;
   return STDA_OK;
 }

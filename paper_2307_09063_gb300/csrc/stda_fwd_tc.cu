@@ -5,12 +5,13 @@
 // One kernel per network level; one CTA per band of rows of one window,
 // always spanning the full map width. Per CTA:
 //  1. Stage the block input x (previous block output x ECA weights, plus the
-//     skip operand for decoders; for encoder block 1 the stem conv computed
-//     from the three raw frames) into shared memory as bf16 "planes" in the
+//     skip operand for decoders) into shared memory as bf16 "planes" in the
 //     no-swizzle K-major core-matrix layout [channel group][pixel][8 ch]
 //     with zero margins. Encoder inputs are split into four polyphase planes
 //     (even/odd row x even/odd column), so that the stride-2 3x3 convolution
-//     reads each tap at a unit-stride shifted pixel.
+//     reads each tap at a unit-stride shifted pixel. Encoder block 1
+//     (k_enc1_tc) instead stages the raw maps with TMA tensor copies and
+//     computes the stem conv as a GEMM on the tensor cores into its planes.
 //  2. Stage 1 (Eqs. mobile_*_stage1, BN folded into one depthwise 3x3 +
 //     bias + ReLU) on the CUDA cores into a second set of planes.
 //  3. Stage 2 (Eqs. mobile_*_stage2) on the tensor cores: the GEMM rows are
@@ -21,6 +22,8 @@
 //     Main and residual branches accumulate into separate TMEM columns.
 //  4. Epilogue: TMEM -> registers, ReLU(main + BN shift) + residual + bias,
 //     bf16 NHWC store, per-band channel sums for the next ECA.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -385,15 +388,6 @@ struct Misc {
   }
 };
 
-// 16-byte asynchronous global -> shared copy (zero-fill when !valid; the
-// source is then not read), and waits for this thread's copies.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Stage-1 weights of tap t, channels 4q .. 4q + 3 of group g (layout
 // [tap][quad][group][4]).
@@ -494,16 +488,14 @@ __device__ __forceinline__ bool run_tiles(const TcArgs& a, const Misc& M, uint32
 }
 
 // ---------------------------------------------------------------- encoder
-template <int CI, bool STEM, bool F8, int NF = 3>
+template <int CI, bool F8>
 __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   using OP = Op<F8>;
   constexpr int CG = OP::CG, G = CI / CG, CO = 2 * CI, NP = CO;
-  static_assert(!(STEM && F8), "the stem block runs in bf16");
   extern __shared__ __align__(1024) unsigned char sm[];
   const int nsteps = a.nsteps, T = a.L.terms;
-  const int in_bytes = STEM ? NF * (2 * a.band + 6) * (a.w + 16) * 2 : 0;
   constexpr MiscLayout ML = misc_layout(CI, true, F8);
-  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, in_bytes, T, ML.total);
+  const Smem L = smem_layout(nsteps, NP, 4 * G, a.PIXA, 0, T, ML.total);
   const size_t lo_off = (size_t)4 * G * a.PIXA * 16;  // low-term planes follow the high-term ones
   Misc M(sm + L.off_misc, ML, CI);
   unsigned char* x0 = sm + L.off_x0;
@@ -538,10 +530,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
     M.sm[i] = F8 ? a.L.swm[i] : 1.f;
     M.sr[i] = F8 ? a.L.swr[i] : 1.f;
   }
-  if (STEM) {
-    for (int i = tid; i < 72 * NF; i += blockDim.x) M.stw[i] = a.stem_w[i];
-    for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
-  }
   if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
   fence_before_sync();
   __syncthreads();
@@ -550,128 +538,54 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
   const int items = a.tiles_per_window * a.nwin;
   bool failed = false;
-  // stem: the NF raw maps of an item's rows (with halo) are copied
-  // asynchronously into the input staging area, zero outside the map; the
-  // next item's copy is issued as soon as the stem has consumed this one
-  auto stem_fetch = [&](int it) {
-    if (!STEM || it >= items) return;
-    const int bb = it / a.tiles_per_window, oy = (it % a.tiles_per_window) * TY;
-    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy - 3, nch = CW / 8;
-    __nv_bfloat16* sin = (__nv_bfloat16*)(sm + L.off_in);
-    const __nv_bfloat16* in = a.in + (size_t)bb * NF * h * w;
-    for (int i = tid; i < NF * RI * nch; i += blockDim.x) {
-      const int c = i / (RI * nch), r = (i / nch) % RI, x = (i % nch) * 8 - 8, y = yi0 + r;
-      const bool ok = y >= 0 && y < h && x >= 0 && x < w;
-      cp_async16(sin + (size_t)i * 8, ok ? (const void*)(in + ((size_t)c * h + y) * w + x) : (const void*)in, ok);
-    }
-    cp_async_commit();
-  };
-  stem_fetch(blockIdx.x);
 
   // persistent loop over (window, band) items
   for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int oy0 = band * TY;
   zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
-  if (!STEM)
-    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
+  eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
   // 1. block input x into the four phase planes: plane (py, px) holds
   // x[2r + py][2s + px] at local row r - (oy0 - 1), column s + 1.
   const int y_lo = max(0, 2 * oy0 - 2), y_hi = min(h - 1, 2 * oy0 + 2 * TY + 1);
-  if (STEM) {
-    const int RI = 2 * TY + 6, CW = w + 16, yi0 = 2 * oy0 - 3;
-    const __nv_bfloat16* sin = (const __nv_bfloat16*)(sm + L.off_in);
-    cp_async_wait_all();  // this item's rows (issued during the previous item)
-    __syncthreads();
-    // stem conv NF -> 8: four horizontally adjacent positions per thread share
-    // the weight loads; channel pairs go through packed FP32 FMAs
-    const int w4 = w / 4;
-    for (int i = tid; i < (y_hi - y_lo + 1) * w4; i += blockDim.x) {
-      const int y = y_lo + i / w4, x = 4 * (i % w4);
-      float2 acc[4][4];
+  // the band's rows are contiguous in NHWC. Item i = (pixel pair i / G,
+  // group i % G): pixels (y, x) and (y, x + 1), x even, land in the two
+  // column-parity planes at the same plane pixel, so one store
+  // instruction touches G planes at consecutive pixels
+  const __nv_bfloat16* in = a.in + ((size_t)b * h + y_lo) * w * CI;
+  const int w2 = w / 2, n = (y_hi - y_lo + 1) * w2 * G;
+  for (int base = tid; base < n; base += 2 * blockDim.x) {
+    uint4 v[2][2][CG / 8];
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[p][k] = make_float2(M.stb[2 * k], M.stb[2 * k + 1]);
-#pragma unroll
-      for (int c = 0; c < NF; ++c)
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-          // columns x - 1 .. x + 4 sit at row[x + 7 .. x + 12]: one 4-, one
-          // 8- and one 4-byte load (rows are 8-byte aligned, x % 4 == 0)
-          const __nv_bfloat16* row = sin + (c * RI + y - yi0 + ky - 1) * CW + x;
-          const uint32_t l = *(const uint32_t*)(row + 6), r = *(const uint32_t*)(row + 12);
-          const uint2 m = *(const uint2*)(row + 8);
-          const float v[6] = {__uint_as_float(l & 0xFFFF0000u), __uint_as_float(m.x << 16),
-                              __uint_as_float(m.x & 0xFFFF0000u), __uint_as_float(m.y << 16),
-                              __uint_as_float(m.y & 0xFFFF0000u), __uint_as_float(r << 16)};
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
-            const float4 wa = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8];
-            const float4 wb = *(const float4*)&M.stw[(c * 9 + ky * 3 + kx) * 8 + 4];
-            const float2 wv[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
-                                  make_float2(wb.z, wb.w)};
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const float2 vv = make_float2(v[p + kx], v[p + kx]);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) ffma2(acc[p][k], vv, wv[k]);
-            }
-          }
-        }
-      const int prow = ((y >> 1) - oy0 + 1) * WP, pl = (y & 1) * 2;
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        float o[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          o[2 * k] = fmaxf(acc[p][k].x, 0.f);
-          o[2 * k + 1] = fmaxf(acc[p][k].y, 0.f);
-        }
-        store_px<F8>(px(x0, pl + (p & 1), prow + ((x + p) >> 1) + 1), o, T, lo_off);
+    for (int u = 0; u < 2; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < n) {
+        const __nv_bfloat16* src = in + ((size_t)(i / G) * 2 * G + i % G) * CG;
+        load_cg<CG>(src, v[u][0]);
+        load_cg<CG>(src + CI, v[u][1]);
       }
     }
-  } else {
-    // the band's rows are contiguous in NHWC. Item i = (pixel pair i / G,
-    // group i % G): pixels (y, x) and (y, x + 1), x even, land in the two
-    // column-parity planes at the same plane pixel, so one store
-    // instruction touches G planes at consecutive pixels
-    const __nv_bfloat16* in = a.in + ((size_t)b * h + y_lo) * w * CI;
-    const int w2 = w / 2, n = (y_hi - y_lo + 1) * w2 * G;
-    for (int base = tid; base < n; base += 2 * blockDim.x) {
-      uint4 v[2][2][CG / 8];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = base + u * blockDim.x;
-        if (i < n) {
-          const __nv_bfloat16* src = in + ((size_t)(i / G) * 2 * G + i % G) * CG;
-          load_cg<CG>(src, v[u][0]);
-          load_cg<CG>(src + CI, v[u][1]);
-        }
-      }
+    for (int u = 0; u < 2; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i >= n) continue;
+      const int g = i % G, pos = i / G, y = y_lo + pos / w2, xp = pos % w2;
+      const int p = ((y >> 1) - oy0 + 1) * WP + xp + 1;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = base + u * blockDim.x;
-        if (i >= n) continue;
-        const int g = i % G, pos = i / G, y = y_lo + pos / w2, xp = pos % w2;
-        const int p = ((y >> 1) - oy0 + 1) * WP + xp + 1;
+      for (int q = 0; q < 2; ++q) {
+        float f[CG];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float f[CG];
+        for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(v[u][q][k], f + 8 * k);
 #pragma unroll
-          for (int k = 0; k < CG / 8; ++k) bf16x8_to_f32(v[u][q][k], f + 8 * k);
-#pragma unroll
-          for (int c = 0; c < CG; ++c) f[c] *= M.sa[g * CG + c];
-          store_px<F8>(px(x0, ((y & 1) * 2 + q) * G + g, p), f, T, lo_off);
-        }
+        for (int c = 0; c < CG; ++c) f[c] *= M.sa[g * CG + c];
+        store_px<F8>(px(x0, ((y & 1) * 2 + q) * G + g, p), f, T, lo_off);
       }
     }
   }
   __syncthreads();
-  stem_fetch(item + gridDim.x);  // the staging area is free again
   // 2. stage 1 at the rows the stride-2 taps read: y in [2 oy0 - 1, 2 oy0 + 2 TY - 1].
   // Item = (pixel pair (y, x), (y, x + 1) with x even, group g): the pair
   // reads columns x - 1 .. x + 2 of three rows, 12 plane pixels for 18 taps.
@@ -770,7 +684,292 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   }
   __syncthreads();
   }  // item loop
-  if (STEM) cp_async_wait_all();  // copies issued for an item past a failure
+  if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// ------------------------------------------- encoder block 1, stem on tcgen05
+// Shared-memory carve-up of k_enc1_tc, identical on host and device: packed
+// stage-2 weights (main, residual) and stem weights, the stem-output planes
+// x0 (four polyphase planes), the stage-1 planes x1 (which first hold the
+// stem GEMM's A operand S: dead once the stem tiles are drained, before
+// stage 1 writes x1), the TMA staging of the raw maps, the misc area, and
+// the TMA barrier and stem descriptor table.
+struct E1Smem {
+  int wbytes, planes_bytes, s_bytes, x1_bytes, raw_bytes;
+  int off_wm, off_wr, off_ws, off_x0, off_x1, off_raw, off_misc, off_extra, total;
+};
+constexpr int kStemWBytes = 3 * 2 * 32 * 16;  // [dy 3][K half 2][N 32][8 bf16]
+// A TMA box lands at a 1024-byte aligned offset (box_bytes = frames x rows x
+// columns x 2 bytes each, nbox boxes side by side in the staging area).
+__host__ __device__ inline int box_stride(int box_bytes) { return (box_bytes + 1023) / 1024 * 1024; }
+__host__ __device__ inline E1Smem enc1_smem(int nsteps, int PIXA, int PS, int nbox, int box_bytes, int misc_bytes) {
+  E1Smem s;
+  s.wbytes = nsteps * 2 * 16 * 16;  // N = 16 output channels
+  s.planes_bytes = (4 * PIXA * 16 + 127) / 128 * 128;
+  s.s_bytes = 2 * PS * 16;
+  s.x1_bytes = ((s.planes_bytes > s.s_bytes ? s.planes_bytes : s.s_bytes) + 127) / 128 * 128;
+  s.raw_bytes = nbox * box_stride(box_bytes);
+  s.off_wm = 0;
+  s.off_wr = s.wbytes;
+  s.off_ws = 2 * s.wbytes;
+  s.off_x0 = s.off_ws + kStemWBytes;
+  s.off_x1 = s.off_x0 + s.planes_bytes;
+  s.off_raw = (s.off_x1 + s.x1_bytes + 1023) / 1024 * 1024;
+  s.off_misc = s.off_raw + s.raw_bytes;
+  s.off_extra = s.off_misc + misc_bytes;
+  s.total = s.off_extra + 64;
+  return s;
+}
+
+// Encoder block 1 with the stem conv (NF maps -> 8 channels) as an implicit
+// GEMM on the tensor cores. Per (window, band) item:
+//  1. TMA (issued during the previous item) has copied the NF raw maps of
+//     the band's input rows, with an 8-column zero margin on either side and
+//     zero rows outside the map, into the staging area (Eq. concat_operation
+//     is the channel stacking of the NF maps).
+//  2. The staging is rearranged into S, one 32-byte row per pixel pair
+//     (x, x + 1), x even: K slot 4 f + j = map f at column x - 1 + j (two
+//     8-element K planes). A 128-pair tile of the stem is three MMAs
+//     (M = 128 pairs, K = 16, N = 32: 8 channels x 2 columns, for the bf16
+//     high part of the weights and again for their bf16 remainder, so the
+//     stem keeps FP32-level weights), one per kernel row, whose A
+//     descriptor starts one S row up / down.
+//  3. The stem tiles are drained (bias, ReLU) straight into the polyphase
+//     planes x0: the pair's two columns land in the even- and odd-column
+//     planes at the same plane pixel.
+//  4. Stage 1 (FFMA) and stage 2 (tcgen05) as in k_enc_tc.
+template <int NF>
+__global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int CI = 8, CG = 8, G = 1, CO = 16, NP = 16;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int nsteps = a.nsteps;
+  constexpr MiscLayout ML = misc_layout(CI, true, false);
+  const int TY = a.band, h = a.h, w = a.w, ho = h / 2, wo = w / 2, WP = a.WP, PIXA = a.PIXA;
+  const int RS = 2 * TY + 6, RP = w / 2, PS = a.PS, BW = a.BW;
+  const int BOXE = box_stride(NF * RS * BW * 2) / 2;  // elements between TMA boxes in the staging area
+  const E1Smem L = enc1_smem(nsteps, PIXA, PS, a.nbox, NF * RS * BW * 2, ML.total);
+  Misc M(sm + L.off_misc, ML, CI);
+  uint64_t* tbar = (uint64_t*)(sm + L.off_extra);
+  uint2* stab = (uint2*)(sm + L.off_extra + 16);
+  unsigned char* x0 = sm + L.off_x0;
+  unsigned char* x1 = sm + L.off_x1;
+  unsigned char* S = x1;
+  const __nv_bfloat16* raw = (const __nv_bfloat16*)(sm + L.off_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto px = [&](unsigned char* base, int pl, int p) { return (uint4*)(base + ((size_t)pl * PIXA + p) * 16); };
+
+  if (tid == 0) {
+    for (int k = 0; k < 2 * a.nbuf; ++k) mbar_init(M.bar + k, 1);
+    mbar_init(tbar, 1);
+    mbar_fence_init();
+  }
+  copy_to_smem(sm + L.off_wm, a.L.wm, L.wbytes);
+  copy_to_smem(sm + L.off_wr, a.L.wr, L.wbytes);
+  copy_to_smem(sm + L.off_ws, a.stem_pk, kStemWBytes);
+  const int m_lo = WP + 1;
+  fill_desc_table<false>(M.dtab, a.L.ks, nsteps, 1, NP, m_lo, WP, PIXA, smem_u32(x1), smem_u32(x0),
+                         smem_u32(sm + L.off_wm), smem_u32(sm + L.off_wr));
+  // stem K-step k (kernel row dy = k - 1): tile 0 starts at S row 1, so its
+  // A rows for row dy start at pair k * RP; the second K plane is PS pairs on
+  if (tid < 3) {
+    const uint64_t da = desc(smem_u32(S) + (uint32_t)(tid * RP) * 16u, (uint32_t)PS * 16u, 128);
+    const uint64_t db = desc(smem_u32(sm + L.off_ws) + (uint32_t)tid * 1024u, 512u, 128);
+    stab[tid] = make_uint2((uint32_t)da, (uint32_t)db);
+  }
+  for (int i = tid; i < 9 * CI; i += blockDim.x) {
+    const int t = i / CI, gq = (i % CI) / 4, e = i % 4;
+    M.dw[((t * (CG / 4) + gq % (CG / 4)) * G + gq / (CG / 4)) * 4 + e] = a.dw[i];
+  }
+  for (int i = tid; i < CI; i += blockDim.x) M.dwb[i] = a.dwb[i];
+  for (int i = tid; i < CO; i += blockDim.x) {
+    M.b2[i] = a.b2[i];
+    M.rb[i] = a.rb[i];
+  }
+  for (int i = tid; i < 8; i += blockDim.x) M.stb[i] = a.stem_b[i];
+  if (warp == 0) tmem_alloc(M.tslot, a.tmem_cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *M.tslot;
+  uint32_t phases = 0, tpar = 0;
+  const int items = a.tiles_per_window * a.nwin;
+  bool failed = false, in_flight = false;
+  // the NF maps of item it's input rows 2 oy0 - 3 .. 2 oy0 + 2 TY + 2 (RS
+  // rows), columns -8 .. w + 7, as nbox boxes of BW columns
+  auto fetch = [&](int it) {
+    if (it >= items) return;
+    in_flight = true;
+    if (tid != 0) return;
+    const int bb = it / a.tiles_per_window, oy = (it % a.tiles_per_window) * TY;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(tbar, (uint32_t)a.raw_bytes);
+    for (int i = 0; i < a.nbox; ++i)
+      tma_load_3d((void*)(raw + (size_t)i * BOXE), &tmap, -8 + i * BW, 2 * oy - 3, bb * NF, tbar);
+  };
+  fetch(blockIdx.x);
+
+  for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+  const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
+  const int oy0 = band * TY, yi0 = 2 * oy0 - 3;
+  zero_smem(x0, L.planes_bytes);
+  for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
+  // 1. this item's maps (TMA issued during the previous item)
+  const bool got = mbar_wait(tbar, tpar, a.wait_polls);
+  tpar ^= 1u;
+  if (__syncthreads_or(!got)) {
+    failed = true;
+    break;
+  }
+  in_flight = false;
+  // 2. S[r][j] for input row yi0 + r, pair j (columns 2 j, 2 j + 1): per map
+  // the words at columns 2j-2, 2j, 2j+2 give slots (2j-1, 2j) and (2j+1, 2j+2)
+  for (int i = tid; i < RS * RP; i += blockDim.x) {
+    const int r = i / RP, j = i % RP;
+    uint32_t v[8];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (f < NF) {
+        uint32_t wd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int q = 2 * j + 2 * k + 6;  // staging column of map column 2 j + 2 k - 2
+          wd[k] = *(const uint32_t*)(raw + (size_t)(q / BW) * BOXE + ((size_t)f * RS + r) * BW + q % BW);
+        }
+        v[2 * f] = __byte_perm(wd[0], wd[1], 0x5432);
+        v[2 * f + 1] = __byte_perm(wd[1], wd[2], 0x5432);
+      } else {
+        v[2 * f] = v[2 * f + 1] = 0u;
+      }
+    }
+    *(uint4*)(S + ((size_t)r * RP + j) * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+    *(uint4*)(S + ((size_t)PS + r * RP + j) * 16) = make_uint4(v[4], v[5], v[6], v[7]);
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  fetch(item + gridDim.x);  // the staging area is free again
+  // 3. stem tiles: pair m = RP + 128 i + row of the tile, S row m / RP = input
+  // row y - yi0; rows y outside the map stay zero in x0 (the stem's zero
+  // padding as seen by stage 1 and the residual conv)
+  const int cpt = 2 * NP;
+  bool ok = run_tiles<false>(
+      a, M, tmem, phases, cpt, stab, a.ntile_s, 3, 1, 32, 1, 0u, 0u, [&](int i, uint32_t col, int, int) {
+        const int m = RP + 128 * i + (warp & 3) * 32 + lane, r = m / RP, j = m % RP, y = yi0 + r;
+        float v[16], lo[16];
+        ld16(lane_addr(tmem, warp, col), v);
+        ld16(lane_addr(tmem, warp, col + 16), lo);
+        ld_wait();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += lo[k];  // high + low weight terms
+        if (r >= 1 && r <= 2 * TY + 4 && y >= 0 && y < h) {
+          float o0[8], o1[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            o0[k] = fmaxf(v[k] + M.stb[k], 0.f);
+            o1[k] = fmaxf(v[8 + k] + M.stb[k], 0.f);
+          }
+          const int p = ((y >> 1) - oy0 + 1) * WP + j + 1, pl = (y & 1) * 2;
+          *px(x0, pl, p) = f32_to_bf16x8(o0);
+          *px(x0, pl + 1, p) = f32_to_bf16x8(o1);
+        }
+      });
+  fence_before_sync();
+  failed = __syncthreads_or(!ok);
+  fence_after_sync();
+  if (failed) break;
+  zero_smem(x1, L.planes_bytes);  // S is dead: x1 becomes the stage-1 planes
+  __syncthreads();
+  // 4a. stage 1 at the rows the stride-2 taps read, a pixel pair per thread
+  // (as in k_enc_tc)
+  {
+    const int y1_lo = max(0, 2 * oy0 - 1), y1_hi = min(h - 1, 2 * oy0 + 2 * TY - 1), w2 = w / 2;
+    for (int i = tid; i < (y1_hi - y1_lo + 1) * w2; i += blockDim.x) {
+      const int y = y1_lo + i / w2, x = 2 * (i % w2);
+      float2 acc0[CG / 2], acc1[CG / 2];
+#pragma unroll
+      for (int c = 0; c < CG / 2; ++c) {
+        acc0[c] = make_float2(M.dwb[2 * c], M.dwb[2 * c + 1]);
+        acc1[c] = acc0[c];
+      }
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const int yy = y + dy - 1, prow = ((yy >> 1) - oy0 + 1) * WP + 1, pr = (yy & 1) * 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int xx = x - 1 + k;
+          float f[CG];
+          bf16x8_to_f32(*px(x0, pr + (xx & 1), prow + (xx >> 1)), f);
+          if (k <= 2) {
+#pragma unroll
+            for (int q = 0; q < CG / 4; ++q) {
+              const float4 wv = dw_quad<CG>(M.dw, dy * 3 + k, q, 0, G);
+              ffma2(acc0[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+              ffma2(acc0[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
+            }
+          }
+          if (k >= 1) {
+#pragma unroll
+            for (int q = 0; q < CG / 4; ++q) {
+              const float4 wv = dw_quad<CG>(M.dw, dy * 3 + k - 1, q, 0, G);
+              ffma2(acc1[2 * q], make_float2(f[4 * q], f[4 * q + 1]), make_float2(wv.x, wv.y));
+              ffma2(acc1[2 * q + 1], make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(wv.z, wv.w));
+            }
+          }
+        }
+      }
+      const int p = ((y >> 1) - oy0 + 1) * WP + x / 2 + 1;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float o[CG];
+#pragma unroll
+        for (int c = 0; c < CG / 2; ++c) {
+          const float2 v2 = q ? acc1[c] : acc0[c];
+          o[2 * c] = fmaxf(v2.x, 0.f);
+          o[2 * c + 1] = fmaxf(v2.y, 0.f);
+        }
+        *px(x1, (y & 1) * 2 + q, p) = f32_to_bf16x8(o);
+      }
+    }
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  // 4b. stage 2 on the tensor cores and the epilogue (as in k_enc_tc)
+  ok = run_tiles<false>(
+      a, M, tmem, phases, cpt, M.dtab, a.ntile, nsteps, 2, NP, 1, 0u, 0u, [&](int i, uint32_t col, int, int) {
+        int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
+        int lr = m / WP, lc = m % WP, oy = oy0 + lr - 1, ox = lc - 1;
+        bool valid = lr >= 1 && lr <= TY && oy < ho && ox >= 0 && ox < wo;
+        __nv_bfloat16* dst = a.out + (((size_t)b * ho + oy) * wo + ox) * CO;
+        float mv[16], rv[16];
+        ld16(lane_addr(tmem, warp, col), mv);
+        ld16(lane_addr(tmem, warp, col + NP), rv);
+        ld_wait();
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = valid ? epi(mv[j], rv[j], 1.f, 1.f, M.b2[j], M.rb[j]) : 0.f;
+        if (valid) {
+          *(uint4*)(dst) = f32_to_bf16x8(o);
+          *(uint4*)(dst + 8) = f32_to_bf16x8(o + 8);
+        }
+        warp_sums_to<16>(o, &M.red[warp * CO]);
+      });
+  fence_before_sync();
+  failed = __syncthreads_or(!ok);
+  fence_after_sync();
+  if (failed) break;
+  float* part = a.part + ((size_t)b * a.tiles_per_window + band) * CO;
+  for (int c = tid; c < CO; c += blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += M.red[k * CO + c];
+    part[c] = s;
+  }
+  __syncthreads();
+  }  // item loop
+  if (failed && tid == 0) atomicExch(a.status, (int)STDA_ERR_TIMEOUT);
+  if (in_flight) mbar_wait(tbar, tpar);  // a copy issued for an item past a failure
   if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
@@ -982,6 +1181,7 @@ int steps_per_acc(int b, bool f8) { return k_steps_per_acc(kBlkCin[b], kBlkEnc[b
 struct Geo {
   int band, ntile, WP, PIXA, smem, threads, nbuf, nslot, gpb;
   uint32_t cols;
+  int ntile_s, PS, nbox, BW, raw_bytes;  // encoder block 1 (stem GEMM, TMA staging)
 };
 
 // TMEM buffers: one per warp group where the column budget allows, then a
@@ -1024,8 +1224,21 @@ Geo encoder_geo_at(int b, bool f8, int terms, int w, int TY, int pass, int frame
   g.ntile = cdiv(count, 128);
   g.PIXA = std::max((TY + 2) * g.WP, m_lo + 128 * g.ntile + 1);
   g.PIXA = (g.PIXA + 7) / 8 * 8 + plane_skew(G);
-  const int in_bytes = stem ? frames * (2 * TY + 6) * (w + 16) * 2 : 0;
-  g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, in_bytes, terms, misc_layout(CI, true, f8).total).total;
+  if (stem) {
+    // stem GEMM over the pixel pairs of input rows 2 oy0 - 2 .. 2 oy0 + 2 TY + 1
+    // (S rows 1 .. 2 TY + 4 of RS = 2 TY + 6); the last tile and the row
+    // shift dy = +1 read up to RP + 128 ntile_s + RP pairs of each K plane
+    const int RS = 2 * TY + 6, RP = w / 2;
+    g.ntile_s = cdiv((2 * TY + 4) * RP, 128);
+    g.PS = (std::max(RS * RP, 2 * RP + 128 * g.ntile_s) + 7) / 8 * 8;
+    // TMA boxes: at most 256 columns each, a multiple of 8 columns (16 bytes)
+    g.nbox = cdiv(w + 16, 256);
+    g.BW = (cdiv(w + 16, g.nbox) + 7) / 8 * 8;
+    g.raw_bytes = g.nbox * frames * RS * g.BW * 2;  // bytes the TMA boxes of one item deliver
+    g.smem = enc1_smem(nsteps, g.PIXA, g.PS, g.nbox, frames * RS * g.BW * 2, misc_layout(CI, true, f8).total).total;
+  } else {
+    g.smem = smem_layout(nsteps, CO, 4 * G, g.PIXA, 0, terms, misc_layout(CI, true, f8).total).total;
+  }
   g.threads = pass == 0 ? 256 : 512;
   pick_buffers(g, 2 * CO, pass == 0 ? 256 : 512);
   if (!g.nbuf || g.smem > (pass == 0 ? kTcHalfSmem : kTcMaxSmem)) g.band = 0;
@@ -1077,16 +1290,51 @@ int sm_count() {
 
 // Persistent launch: one CTA per SM (two where the geometry allows), each
 // looping over (window, band) items.
-template <typename K>
-cudaError_t launch(K kern, const Geo& g, int B, const TcArgs& a, cudaStream_t st) {
+template <typename K, typename... X>
+cudaError_t launch(K kern, const Geo& g, int B, const TcArgs& a, cudaStream_t st, const X&... extra) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
   if (e) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   const int per_sm = g.threads == 256 ? 2 : 1;
   const long items = (long)a.tiles_per_window * B;
   const int grid = (int)std::min<long>(items, (long)sm_count() * per_sm);
-  kern<<<grid, g.threads, g.smem, st>>>(a);
+  kern<<<grid, g.threads, g.smem, st>>>(a, extra...);
   return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query, so the library does not link libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of the raw input [B][frames][H][W] bf16 as a 3-D tensor
+// (W, H, B * frames) with boxes of BW columns x RS rows x frames maps; zero
+// fill outside the tensor (the map's padding for the stem conv).
+cudaError_t raw_tensor_map(CUtensorMap* m, const __nv_bfloat16* in, int B, int frames, int H, int W, int BW,
+                           int RS) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B * frames};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)H * W * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)RS, (cuuint32_t)frames};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)in, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -1100,7 +1348,7 @@ int tap_phase(int k) { return k == 1 ? 0 : 1; }
 int tap_shift(int k) { return k == 0 ? -1 : 0; }
 }  // namespace
 
-void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int f8_terms,
+void pack_tc(const float* folded, const FoldedOffsets& off, int frames, const bool* f8, int f8_terms,
              std::vector<unsigned char>* blob, TcPackOffsets* po) {
   std::vector<unsigned char> w;  // packed operands, then scales, then K-step tables
   std::vector<float> scales;
@@ -1109,6 +1357,33 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
   auto align128 = [&]() {
     while (w.size() % 128) w.push_back(0);
   };
+  auto push_bf16 = [&](float v) {
+    __nv_bfloat16 q = __float2bfloat16(v);
+    unsigned char bytes[2];
+    std::memcpy(bytes, &q, 2);
+    w.push_back(bytes[0]);
+    w.push_back(bytes[1]);
+  };
+  // Stem (conv3x3 frames -> 8, BN folded) as the B operand of the stem GEMM
+  // of encoder block 1. Its A rows are pixel pairs (x, x + 1), x even; K slot
+  // s = 4 f + j holds map f at column x - 1 + j (16 slots, two 8-element K
+  // halves), one K-step per kernel row dy; N = 32 columns, n = 16 t + 8 q + o:
+  // output channel o at column x + q, for term t (0: the weight rounded to
+  // bf16, 1: the bf16 rounding of its remainder). So column x + q reads
+  // slot j with dx = j - 1 - q.
+  po->stem = w.size();
+  for (int k = 0; k < 3; ++k)
+    for (int hf = 0; hf < 2; ++hf)
+      for (int n = 0; n < 32; ++n)
+        for (int c = 0; c < 8; ++c) {
+          const int sl = hf * 8 + c, f = sl / 4, j = sl % 4, t = n / 16, q = (n / 8) % 2, o = n % 8,
+                    dx = j - 1 - q;
+          const bool live = f < frames && dx >= -1 && dx <= 1;
+          const float v = live ? folded[off.stem_w + (f * 9 + k * 3 + dx + 1) * 8 + o] : 0.f;
+          const float hi = __bfloat162float(__float2bfloat16(v));
+          push_bf16(t == 0 ? hi : v - hi);
+        }
+  align128();
   for (int b = 0; b < kNumBlocks; ++b) {
     const int ci = kBlkCin[b], co = kBlkCout[b], CG = f8[b] ? 16 : 8, G = ci / CG;
     const bool enc = kBlkEnc[b], stack = !enc && dec_stacked(ci);
@@ -1258,6 +1533,7 @@ void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int 
 
 TcWeights tc_weights_from(const unsigned char* base, const TcPackOffsets& po) {
   TcWeights t;
+  t.stem = base + po.stem;
   for (int b = 0; b < kNumBlocks; ++b)
     t.layer[b] = TcLayer{base + po.wm[b], base + po.wr[b], (const KStep*)(base + po.ks[b]),
                          (const float*)(base + po.swm[b]), (const float*)(base + po.swr[b]), po.f8[b],
@@ -1314,22 +1590,32 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     a.part = s.part[l];
     a.status = status;
     a.wait_polls = wait_polls;
+    a.ntile_s = g.ntile_s;
+    a.PS = g.PS;
+    a.nbox = g.nbox;
+    a.BW = g.BW;
+    a.raw_bytes = g.raw_bytes;
+    a.stem_pk = tw.stem;
     const int rows = kBlkEnc[l] ? h / 2 : h;
     a.tiles_per_window = cdiv(rows, g.band);
     a.nwin = B;
     tiles[l] = a.tiles_per_window;
     hook->begin(K_ENC1 + l, st);
     switch (l * 2 + (f8 ? 1 : 0)) {
-      case 0:
-        e = w.frames == 2   ? launch(k_enc_tc<8, true, false, 2>, g, B, a, st)
-            : w.frames == 4 ? launch(k_enc_tc<8, true, false, 4>, g, B, a, st)
-            : w.frames == 3 ? launch(k_enc_tc<8, true, false, 3>, g, B, a, st)
+      case 0: {
+        CUtensorMap tm;
+        e = raw_tensor_map(&tm, in, B, w.frames, H, W, g.BW, 2 * g.band + 6);
+        if (e) break;
+        e = w.frames == 2   ? launch(k_enc1_tc<2>, g, B, a, st, tm)
+            : w.frames == 4 ? launch(k_enc1_tc<4>, g, B, a, st, tm)
+            : w.frames == 3 ? launch(k_enc1_tc<3>, g, B, a, st, tm)
                             : cudaErrorInvalidValue;
         break;
-      case 2: e = launch(k_enc_tc<16, false, false>, g, B, a, st); break;
-      case 3: e = launch(k_enc_tc<16, false, true>, g, B, a, st); break;
-      case 4: e = launch(k_enc_tc<32, false, false>, g, B, a, st); break;
-      case 5: e = launch(k_enc_tc<32, false, true>, g, B, a, st); break;
+      }
+      case 2: e = launch(k_enc_tc<16, false>, g, B, a, st); break;
+      case 3: e = launch(k_enc_tc<16, true>, g, B, a, st); break;
+      case 4: e = launch(k_enc_tc<32, false>, g, B, a, st); break;
+      case 5: e = launch(k_enc_tc<32, true>, g, B, a, st); break;
       case 6: e = launch(k_dec_tc<64, false, false>, g, B, a, st); break;
       case 7: e = launch(k_dec_tc<64, false, true>, g, B, a, st); break;
       case 8: e = launch(k_dec_tc<32, true, false>, g, B, a, st); break;

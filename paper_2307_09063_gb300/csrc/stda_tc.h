@@ -30,6 +30,7 @@ struct TcLayer {
   int nsteps;        // K-steps per accumulator
 };
 struct TcWeights {
+  const unsigned char* stem;
   TcLayer layer[6];
 };
 
@@ -62,11 +63,17 @@ struct TcArgs {
   float* part;
   int* status;
   uint32_t wait_polls;  // polls of the tile barrier before a drain wait gives up
+  // encoder block 1 (stem on the tensor cores): stem GEMM tiles per item,
+  // pixel-pair plane stride, TMA boxes per input row and their width
+  // (elements), staged raw bytes per item, packed stem weights
+  int ntile_s, PS, nbox, BW, raw_bytes;
+  const unsigned char* stem_pk;
 };
 
 // Host: packs the folded FP32 weights of every block for the tensor cores.
 // Returns byte offsets (into one device buffer) of each block's tensors.
 struct TcPackOffsets {
+  size_t stem;  // stem weights as tcgen05 B operand: [dy 3][K half 2][N 16][8] bf16
   size_t wm[6], wr[6], ks[6], swm[6], swr[6];
   bool f8[6];
   int terms[6];
@@ -75,7 +82,7 @@ struct TcPackOffsets {
 };
 // f8[b]: block b's stage-2 operands in E4M3 (needs 16 or more input
 // channels), with f8_terms (1 or 2) E4M3 terms per operand.
-void pack_tc(const float* folded, const FoldedOffsets& off, const bool* f8, int f8_terms,
+void pack_tc(const float* folded, const FoldedOffsets& off, int frames, const bool* f8, int f8_terms,
              std::vector<unsigned char>* blob, TcPackOffsets* po);
 TcWeights tc_weights_from(const unsigned char* dev_base, const TcPackOffsets& po);
 

@@ -133,3 +133,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 
 }  // namespace umma
 }  // namespace stda
+
+namespace stda {
+namespace umma {
+
+// ---- TMA (bulk tensor copies) ----
+// Arms the mbarrier for `bytes` of asynchronous transactions (one arrival).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 3-D tiled copy global -> shared of the box at coordinates (x, y, z) of the
+// tensor map (x innermost; out-of-range elements are zero-filled), completing
+// on `bar`. The map must live in kernel-parameter, constant or global memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace umma
+}  // namespace stda
