@@ -60,14 +60,29 @@ __device__ void eca_scales(const float* __restrict__ part, int ntiles, int C,
 
 // Per-channel sums of a tile [npix][C] held in shared memory; one warp per
 // channel, fixed summation order.
-__device__ void tile_sums(const float* tile, int npix, int C, float* __restrict__ out) {
+__device__ void tile_sums(const float* tile, int npix, int C, float* __restrict__ out, int c_lo = 0,
+                          int c_hi = -1) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c = warp; c < C; c += nw) {
+  if (c_hi < 0) c_hi = C;
+  for (int c = c_lo + warp; c < c_hi; c += nw) {
     float a = 0.f;
     for (int p = lane; p < npix; p += 32) a += tile[p * C + c];
 #pragma unroll
     for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) out[c] = a;
+  }
+}
+
+// Stage-2 weights (main then residual, [taps][CI][CO] floats each) of output
+// channel groups g0 .. g0 + ng - 1 into shared memory as [branch][taps][CI][8 ng]:
+// one batch of independent 16-byte loads instead of a dependent chain per
+// thread (what a small grid after a cold cache waits on).
+__device__ void stage_weights(float* s_w, const float* w2, const float* rw, int taps, int CI, int CO, int g0,
+                              int ng) {
+  const int q4 = 2 * ng, n4 = taps * CI * q4;
+  for (int i = threadIdx.x; i < 2 * n4; i += blockDim.x) {
+    const int br = i / n4, j = i % n4, q = j % q4, r = j / q4;
+    ((float4*)s_w)[i] = __ldg((const float4*)((br ? rw : w2) + (size_t)r * CO + g0 * 8 + q * 4));
   }
 }
 
@@ -82,6 +97,8 @@ struct EncArgs {
   int blk;
   T* out;               // [B][H/2][W/2][2 CI]
   float* part;          // [B][tiles][2 CI]
+  int nsplit;           // CTAs per tile, each computing 1 / nsplit of the output channel groups
+  int wsmem;            // stage-2 weights of the CTA's groups copied to shared memory first
 };
 
 template <int CI, int TY, int TX, bool STEM>
@@ -116,9 +133,14 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
   float* s_g = s_o + S::n_o;
   float* s_s = s_g + 64;
   const int b = blockIdx.z, H = a.H, W = a.W, ho = H / 2, wo = W / 2;
-  const int oy0 = blockIdx.y * TY, ox0 = blockIdx.x * TX;
+  const int tx_tile = blockIdx.x / a.nsplit, split = blockIdx.x % a.nsplit;
+  const int oy0 = blockIdx.y * TY, ox0 = tx_tile * TX;
   const int y0 = 2 * oy0 - 2, x0c = 2 * ox0 - 2;
   const BlockW bw = a.w.blk[a.blk];
+  float* s_w = sm + (S::bytes / 4 + 3) / 4 * 4;
+  constexpr int NG = CO / 8;
+  const int ng = NG / a.nsplit, g0 = split * ng;
+  if (a.wsmem) stage_weights(s_w, bw.w2, bw.rw, 9, CI, CO, g0, ng);
 
   if (STEM) {
     const int NF = a.w.frames;
@@ -172,9 +194,9 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
   }
   __syncthreads();
   // stage 2: ReLU(BN(conv3x3-s2 x1)) + conv3x3-s2(x0) + bias
-  constexpr int NPIX = TY * TX, NG = CO / 8;
-  for (int it = threadIdx.x; it < NPIX * NG; it += blockDim.x) {
-    int g = it / NPIX, p = it % NPIX, ty = p / TX, tx = p % TX;
+  constexpr int NPIX = TY * TX;
+  for (int it = threadIdx.x; it < NPIX * ng; it += blockDim.x) {
+    int g = g0 + it / NPIX, p = it % NPIX, ty = p / TX, tx = p % TX;
     float am[8], ar[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -186,13 +208,22 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
       int ky = t / 3, kx = t % 3;
       const float* v1 = s_x1 + ((2 * ty + ky) * S::C1 + 2 * tx + kx) * CIP;
       const float* v0 = s_x0 + ((2 * ty + ky + 1) * S::C0 + 2 * tx + kx + 1) * CIP;
-      const float4* wm = reinterpret_cast<const float4*>(bw.w2 + (size_t)t * CI * CO + g * 8);
-      const float4* wr = reinterpret_cast<const float4*>(bw.rw + (size_t)t * CI * CO + g * 8);
+      const float4 *wm, *wr;
+      int ws;
+      if (a.wsmem) {
+        wm = reinterpret_cast<const float4*>(s_w + ((size_t)t * CI * ng + (g - g0)) * 8);
+        wr = wm + 9 * CI * ng * 2;
+        ws = 2 * ng;
+      } else {
+        wm = reinterpret_cast<const float4*>(bw.w2 + (size_t)t * CI * CO + g * 8);
+        wr = reinterpret_cast<const float4*>(bw.rw + (size_t)t * CI * CO + g * 8);
+        ws = CO / 4;
+      }
 #pragma unroll 4
       for (int ci = 0; ci < CI; ++ci) {
         float x1v = v1[ci], x0v = v0[ci];
-        float4 m0 = __ldg(wm + ci * (CO / 4)), m1 = __ldg(wm + ci * (CO / 4) + 1);
-        float4 r0 = __ldg(wr + ci * (CO / 4)), r1 = __ldg(wr + ci * (CO / 4) + 1);
+        float4 m0 = wm[ci * ws], m1 = wm[ci * ws + 1];
+        float4 r0 = wr[ci * ws], r1 = wr[ci * ws + 1];
         am[0] += x1v * m0.x; am[1] += x1v * m0.y; am[2] += x1v * m0.z; am[3] += x1v * m0.w;
         am[4] += x1v * m1.x; am[5] += x1v * m1.y; am[6] += x1v * m1.z; am[7] += x1v * m1.w;
         ar[0] += x0v * r0.x; ar[1] += x0v * r0.y; ar[2] += x0v * r0.z; ar[3] += x0v * r0.w;
@@ -210,8 +241,9 @@ __global__ void __launch_bounds__(kThreads) k_enc(EncArgs<T> a) {
     }
   }
   __syncthreads();
-  int tiles = gridDim.x * gridDim.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
-  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO);
+  const int tx_tiles = gridDim.x / a.nsplit;
+  int tiles = tx_tiles * gridDim.y, tile = blockIdx.y * tx_tiles + tx_tile;
+  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO, 8 * g0, 8 * (g0 + ng));
 }
 
 template <typename T>
@@ -229,6 +261,8 @@ struct DecArgs {
   int blk;
   T* out;               // [B][2h][2w][CI/2]
   float* part;
+  int nsplit;           // CTAs per tile, each computing 1 / nsplit of the output channel groups
+  int wsmem;            // stage-2 weights of the CTA's groups copied to shared memory first
 };
 
 template <int CI, int TY, int TX>
@@ -262,9 +296,14 @@ __global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
   float* s_sa = s_g + 64;
   float* s_ss = s_sa + 64;
   const int b = blockIdx.z, h = a.h, w = a.w, Ho = 2 * h, Wo = 2 * w;
-  const int Y0 = blockIdx.y * TY, X0 = blockIdx.x * TX;
+  const int tx_tile = blockIdx.x / a.nsplit, split = blockIdx.x % a.nsplit;
+  const int Y0 = blockIdx.y * TY, X0 = tx_tile * TX;
   const int y0 = Y0 / 2 - 2, x0c = X0 / 2 - 2;
   const BlockW bw = a.wt.blk[a.blk];
+  float* s_w = sm + (S::bytes / 4 + 3) / 4 * 4;
+  constexpr int NG = CO / 8;
+  const int ng = NG / a.nsplit, g0 = split * ng;
+  if (a.wsmem) stage_weights(s_w, bw.w2, bw.rw, 16, CI, CO, g0, ng);
   const float inv_n = 1.f / (float)(h * w);
   eca_scales(a.Apart + (size_t)b * a.Atiles * CI, a.Atiles, CI, inv_n, a.Ak3, s_o, s_g, s_sa);
   if (SKIP) eca_scales(a.Spart + (size_t)b * a.Stiles * CI, a.Stiles, CI, inv_n, a.Sk3, s_o, s_g, s_ss);
@@ -293,9 +332,9 @@ __global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
     s_x1[p * CIP + c] = v;
   }
   __syncthreads();
-  constexpr int NPIX = TY * TX, NPH = NPIX / 4, NG = CO / 8;
-  for (int it = threadIdx.x; it < NPIX * NG; it += blockDim.x) {
-    int g = it / NPIX, p = it % NPIX, ph = p / NPH, r = p % NPH;
+  constexpr int NPIX = TY * TX, NPH = NPIX / 4;
+  for (int it = threadIdx.x; it < NPIX * ng; it += blockDim.x) {
+    int g = g0 + it / NPIX, p = it % NPIX, ph = p / NPH, r = p % NPH;
     int py = ph >> 1, px = ph & 1;
     int al = r / (TX / 2), bl = r % (TX / 2);
     int ty = 2 * al + py, tx = 2 * bl + px;
@@ -310,14 +349,23 @@ __global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
       int sy = st >> 1, sx = st & 1, dy = sy - 1 + py, dx = sx - 1 + px;
       const float* v1 = s_x1 + ((al + 1 + dy) * S::C1 + bl + 1 + dx) * CIP;
       const float* v0 = s_x0 + ((al + 2 + dy) * S::C0 + bl + 2 + dx) * CIP;
-      size_t wo = ((size_t)(ph * 4 + st) * CI) * CO + g * 8;
-      const float4* wm = reinterpret_cast<const float4*>(bw.w2 + wo);
-      const float4* wr = reinterpret_cast<const float4*>(bw.rw + wo);
+      const float4 *wm, *wr;
+      int ws;
+      if (a.wsmem) {
+        wm = reinterpret_cast<const float4*>(s_w + ((size_t)(ph * 4 + st) * CI * ng + (g - g0)) * 8);
+        wr = wm + 16 * CI * ng * 2;
+        ws = 2 * ng;
+      } else {
+        size_t wo = ((size_t)(ph * 4 + st) * CI) * CO + g * 8;
+        wm = reinterpret_cast<const float4*>(bw.w2 + wo);
+        wr = reinterpret_cast<const float4*>(bw.rw + wo);
+        ws = CO / 4;
+      }
 #pragma unroll 4
       for (int ci = 0; ci < CI; ++ci) {
         float x1v = v1[ci], x0v = v0[ci];
-        float4 m0 = __ldg(wm + ci * (CO / 4)), m1 = __ldg(wm + ci * (CO / 4) + 1);
-        float4 r0 = __ldg(wr + ci * (CO / 4)), r1 = __ldg(wr + ci * (CO / 4) + 1);
+        float4 m0 = wm[ci * ws], m1 = wm[ci * ws + 1];
+        float4 r0 = wr[ci * ws], r1 = wr[ci * ws + 1];
         am[0] += x1v * m0.x; am[1] += x1v * m0.y; am[2] += x1v * m0.z; am[3] += x1v * m0.w;
         am[4] += x1v * m1.x; am[5] += x1v * m1.y; am[6] += x1v * m1.z; am[7] += x1v * m1.w;
         ar[0] += x0v * r0.x; ar[1] += x0v * r0.y; ar[2] += x0v * r0.z; ar[3] += x0v * r0.w;
@@ -336,8 +384,9 @@ __global__ void __launch_bounds__(kThreads) k_dec(DecArgs<T> a) {
     }
   }
   __syncthreads();
-  int tiles = gridDim.x * gridDim.y, tile = blockIdx.y * gridDim.x + blockIdx.x;
-  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO);
+  const int tx_tiles = gridDim.x / a.nsplit;
+  int tiles = tx_tiles * gridDim.y, tile = blockIdx.y * tx_tiles + tx_tile;
+  tile_sums(s_o, NPIX, CO, a.part + ((size_t)b * tiles + tile) * CO, 8 * g0, 8 * (g0 + ng));
 }
 
 template <typename T>
@@ -431,6 +480,32 @@ int part_tiles(int l, int ho, int wo) {
   return t > ho ? t : ho;
 }
 
+int simt_sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Small grids (a batch of one small map) leave most SMs idle and each CTA
+// runs its output channel groups one after the other: split the groups of a
+// tile over up to `ng` CTAs (a power of two) while the grid stays within two
+// CTAs per SM. Each CTA recomputes the tile's stage 1.
+int group_split(int ctas, int ng) {
+  int n = 1;
+  while (2 * n <= ng && ctas * 2 * n <= 2 * simt_sm_count()) n *= 2;
+  return n;
+}
+
+// Shared-memory bytes of the stage-2 weights of one CTA's channel groups
+// (both branches), and whether they are small enough to stage.
+size_t weight_bytes(int taps, int ci, int co, int ns) { return (size_t)2 * taps * ci * (co / ns) * sizeof(float); }
+bool small_weights(int taps, int ci, int co, int ns) { return weight_bytes(taps, ci, co, ns) <= 96 * 1024; }
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -473,60 +548,78 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
   {
     using Sm = EncSmem<8, 8, 16, true>;
     auto kern = k_enc<T, 8, 8, 16, true>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
-    EncArgs<T> a{in, nullptr, nullptr, 0, H, W, w, 0, (T*)s.act[0], s.part[0]};
+    const int ns = group_split(cdiv(W / 2, 16) * cdiv(H / 2, 8) * B, 16 / 8);
+    const int wsm = cdiv(W / 2, 16) * cdiv(H / 2, 8) * B * ns <= simt_sm_count() && small_weights(9, 8, 16, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(9, 8, 16, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
+    EncArgs<T> a{in, nullptr, nullptr, 0, H, W, w, 0, (T*)s.act[0], s.part[0], ns, wsm};
     hook->begin(K_ENC1, st);
-    kern<<<dim3(cdiv(W / 2, 16), cdiv(H / 2, 8), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W / 2, 16) * ns, cdiv(H / 2, 8), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
     using Sm = EncSmem<16, 8, 16, false>;
     auto kern = k_enc<T, 16, 8, 16, false>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
+    const int ns = group_split(cdiv(W / 4, 16) * cdiv(H / 4, 8) * B, 32 / 8);
+    const int wsm = cdiv(W / 4, 16) * cdiv(H / 4, 8) * B * ns <= simt_sm_count() && small_weights(9, 16, 32, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(9, 16, 32, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
     EncArgs<T> a{(const T*)s.act[0], s.part[0], w.blk[0].eca, s.tiles[0], H / 2, W / 2, w, 1, (T*)s.act[1],
-                 s.part[1]};
+                 s.part[1], ns, wsm};
     hook->begin(K_ENC2, st);
-    kern<<<dim3(cdiv(W / 4, 16), cdiv(H / 4, 8), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W / 4, 16) * ns, cdiv(H / 4, 8), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
     using Sm = EncSmem<32, 8, 8, false>;
     auto kern = k_enc<T, 32, 8, 8, false>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
+    const int ns = group_split(cdiv(W / 8, 8) * cdiv(H / 8, 8) * B, 64 / 8);
+    const int wsm = cdiv(W / 8, 8) * cdiv(H / 8, 8) * B * ns <= simt_sm_count() && small_weights(9, 32, 64, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(9, 32, 64, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
     EncArgs<T> a{(const T*)s.act[1], s.part[1], w.blk[1].eca, s.tiles[1], H / 4, W / 4, w, 2, (T*)s.act[2],
-                 s.part[2]};
+                 s.part[2], ns, wsm};
     hook->begin(K_ENC3, st);
-    kern<<<dim3(cdiv(W / 8, 8), cdiv(H / 8, 8), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W / 8, 8) * ns, cdiv(H / 8, 8), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
     using Sm = DecSmem<64, 8, 16>;
     auto kern = k_dec<T, 64, 8, 16, false>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
+    const int ns = group_split(cdiv(W / 4, 16) * cdiv(H / 4, 8) * B, 32 / 8);
+    const int wsm = cdiv(W / 4, 16) * cdiv(H / 4, 8) * B * ns <= simt_sm_count() && small_weights(16, 64, 32, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(16, 64, 32, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
     DecArgs<T> a{(const T*)s.act[2], s.part[2], w.blk[2].eca, s.tiles[2], nullptr, nullptr, nullptr, 0,
-                 H / 8, W / 8, w, 3, (T*)s.act[3], s.part[3]};
+                 H / 8, W / 8, w, 3, (T*)s.act[3], s.part[3], ns, wsm};
     hook->begin(K_DEC1, st);
-    kern<<<dim3(cdiv(W / 4, 16), cdiv(H / 4, 8), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W / 4, 16) * ns, cdiv(H / 4, 8), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
     using Sm = DecSmem<32, 8, 16>;
     auto kern = k_dec<T, 32, 8, 16, true>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
+    const int ns = group_split(cdiv(W / 2, 16) * cdiv(H / 2, 8) * B, 16 / 8);
+    const int wsm = cdiv(W / 2, 16) * cdiv(H / 2, 8) * B * ns <= simt_sm_count() && small_weights(16, 32, 16, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(16, 32, 16, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
     DecArgs<T> a{(const T*)s.act[3], s.part[3], w.blk[3].eca, s.tiles[3], (const T*)s.act[1], s.part[1],
-                 w.blk[1].eca, s.tiles[1], H / 4, W / 4, w, 4, (T*)s.act[4], s.part[4]};
+                 w.blk[1].eca, s.tiles[1], H / 4, W / 4, w, 4, (T*)s.act[4], s.part[4], ns, wsm};
     hook->begin(K_DEC2, st);
-    kern<<<dim3(cdiv(W / 2, 16), cdiv(H / 2, 8), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W / 2, 16) * ns, cdiv(H / 2, 8), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
     using Sm = DecSmem<16, 16, 16>;
     auto kern = k_dec<T, 16, 16, 16, true>;
-    if ((e = set_smem(kern, Sm::bytes))) return e;
+    const int ns = group_split(cdiv(W, 16) * cdiv(H, 16) * B, 8 / 8);
+    const int wsm = cdiv(W, 16) * cdiv(H, 16) * B * ns <= simt_sm_count() && small_weights(16, 16, 8, ns);
+    const size_t smb = (Sm::bytes + 15) / 16 * 16 + (wsm ? weight_bytes(16, 16, 8, ns) : 0);
+    if ((e = set_smem(kern, smb))) return e;
     DecArgs<T> a{(const T*)s.act[4], s.part[4], w.blk[4].eca, s.tiles[4], (const T*)s.act[0], s.part[0],
-                 w.blk[0].eca, s.tiles[0], H / 2, W / 2, w, 5, (T*)s.act[5], s.part[5]};
+                 w.blk[0].eca, s.tiles[0], H / 2, W / 2, w, 5, (T*)s.act[5], s.part[5], ns, wsm};
     hook->begin(K_DEC3, st);
-    kern<<<dim3(cdiv(W, 16), cdiv(H, 16), B), kThreads, Sm::bytes, st>>>(a);
+    kern<<<dim3(cdiv(W, 16) * ns, cdiv(H, 16), B), kThreads, smb, st>>>(a);
     hook->end(st);
   }
   {
