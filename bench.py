@@ -316,7 +316,26 @@ def run_serving(seconds=3.0, warm=1.0, streams=512, rate=20.0, flush_ms=0.25, se
                 break
     elapsed = seconds
     lat_ms = np.array(lat) * 1e3
+    # saturation: every radar submits its next frame back to back (round
+    # robin); flushes happen when a size class holds 64 windows or a radar
+    # comes round again with its window still pending
+    sat_frames, nsub0 = 0, nsub
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    while sat_frames < 40 * streams:
+        for sidx in range(streams):
+            H, W = size_of[sidx]
+            k = counts[sidx]
+            counts[sidx] += 1
+            frame = pools[(H, W)][(sidx * 7 + k) % len(pools[(H, W)])]
+            if ctx.submit(sidx, frame, outs[(H, W)][nsub % 64], None, stream) == stda.OK:
+                sat_frames += 1
+            nsub += 1
+    ctx.flush(stream)
+    torch.cuda.synchronize()
+    sat = sat_frames / (time.perf_counter() - t1)
     return {"value": done_frames / elapsed, "unit": UNIT, "offered_frames_per_s": streams * rate,
+            "saturation_frames_per_s": sat, "saturation_frames": sat_frames,
             "streams": streams, "mix": "128x64 : 256x128 : 512x256 = 3:2:1", "seconds": seconds,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "max_ms": float(lat_ms.max()), "frames": int(done_frames), "flush_ms": flush_ms,

@@ -398,6 +398,7 @@ struct OutArgs {
   int H, W;
   NetW w;
   T* out;  // [B][H][W]
+  const int* d_nwin;  // bf16 kernel: windows >= *d_nwin are skipped (null: all)
 };
 
 constexpr int kOutTY = 16, kOutTX = 16;
@@ -623,7 +624,7 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
     hook->end(st);
   }
   {
-    OutArgs<T> a{(const T*)s.act[5], s.part[5], w.blk[5].eca, s.tiles[5], H, W, w, out};
+    OutArgs<T> a{(const T*)s.act[5], s.part[5], w.blk[5].eca, s.tiles[5], H, W, w, out, nullptr};
     hook->begin(K_OUT, st);
     k_out<T><<<dim3(cdiv(W, kOutTX), cdiv(H, kOutTY), B), kThreads, 0, st>>>(a);
     hook->end(st);
@@ -671,6 +672,7 @@ __global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a)
   __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
   __shared__ float s_w[72];
   const int b = blockIdx.y, H = a.H, W = a.W, RW = W + 2;
+  if (a.d_nwin && b >= *a.d_nwin) return;
   const int y0 = blockIdx.x * kOutRows, y1 = min(H, y0 + kOutRows);
   const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
   __nv_bfloat16* out = a.out + (size_t)b * H * W;
@@ -729,8 +731,9 @@ __global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a)
 }
 
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
-                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook) {
-  OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out};
+                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook,
+                            const int* d_nwin) {
+  OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out, d_nwin};
   const int threads = std::min(kThreads, (W + 31) / 32 * 32);
   if (W > 2 * threads) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kOutRing * (W + 2) * 16;

@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
   uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
-  const int items = a.tiles_per_window * a.nwin;
+  const int items = a.tiles_per_window * (a.d_nwin ? min(*a.d_nwin, a.nwin) : a.nwin);
   bool failed = false;
 
   // persistent loop over (window, band) items
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
   uint32_t phases = 0, tpar = 0;
-  const int items = a.tiles_per_window * a.nwin;
+  const int items = a.tiles_per_window * (a.d_nwin ? min(*a.d_nwin, a.nwin) : a.nwin);
   bool failed = false, in_flight = false;
   // the NF maps of item it's input rows 2 oy0 - 3 .. 2 oy0 + 2 TY + 2 (RS
   // rows), columns -8 .. w + 7, as nbox boxes of BW columns
@@ -1025,7 +1025,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   fence_after_sync();
   const uint32_t tmem = *M.tslot;
   uint32_t phases = 0;  // bit 2 g + s: parity of barrier (g, s)'s next completion
-  const int items = a.tiles_per_window * a.nwin;
+  const int items = a.tiles_per_window * (a.d_nwin ? min(*a.d_nwin, a.nwin) : a.nwin);
   bool failed = false;
   const float inv_n = 1.f / (float)(h * w);
 
@@ -1543,7 +1543,7 @@ TcWeights tc_weights_from(const unsigned char* base, const TcPackOffsets& po) {
 
 cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* in, __nv_bfloat16* out, int B,
                        int H, int W, const FwdScratch& s, int* status, cudaStream_t st, KernelHook* hook,
-                       int* tiles_out, uint32_t wait_polls) {
+                       int* tiles_out, uint32_t wait_polls, const int* d_nwin) {
   cudaError_t e = cudaSuccess;
   int tiles[6];
   const void* prev = nullptr;
@@ -1599,6 +1599,7 @@ cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* 
     const int rows = kBlkEnc[l] ? h / 2 : h;
     a.tiles_per_window = cdiv(rows, g.band);
     a.nwin = B;
+    a.d_nwin = d_nwin;
     tiles[l] = a.tiles_per_window;
     hook->begin(K_ENC1 + l, st);
     switch (l * 2 + (f8 ? 1 : 0)) {

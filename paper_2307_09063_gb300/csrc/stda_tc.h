@@ -68,6 +68,7 @@ struct TcArgs {
   // (elements), staged raw bytes per item, packed stem weights
   int ntile_s, PS, nbox, BW, raw_bytes;
   const unsigned char* stem_pk;
+  const int* d_nwin;  // windows to process, read on the device (<= nwin), or null for nwin
 };
 
 // Host: packs the folded FP32 weights of every block for the tensor cores.
@@ -95,13 +96,17 @@ constexpr uint32_t kWaitPolls = 1u << 22;
 // wait_polls bounds the epilogue's wait for each tile (0: give up at once,
 // which only tests of the timeout path use); on a timeout the kernel still
 // waits, with the default bound, for the MMAs it issued before it frees its
-// tensor memory, and sets *status to STDA_ERR_TIMEOUT.
+// tensor memory, and sets *status to STDA_ERR_TIMEOUT. With d_nwin the
+// kernels read the number of windows (at most B) from device memory when
+// they start, so a captured graph serves any batch up to B.
 cudaError_t forward_tc(const NetW& w, const TcWeights& tw, const __nv_bfloat16* in, __nv_bfloat16* out, int B,
                        int H, int W, const FwdScratch& s, int* status, cudaStream_t st, KernelHook* hook,
-                       int* tiles_out, uint32_t wait_polls = kWaitPolls);
+                       int* tiles_out, uint32_t wait_polls = kWaitPolls, const int* d_nwin = nullptr);
 
-// Output conv (CUDA cores) over the decoder-3 map, bf16 I/O.
+// Output conv (CUDA cores) over the decoder-3 map, bf16 I/O (windows
+// beyond *d_nwin skipped when d_nwin is given).
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
-                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook);
+                            __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook,
+                            const int* d_nwin = nullptr);
 
 }  // namespace stda

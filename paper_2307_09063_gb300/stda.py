@@ -288,6 +288,10 @@ class Context:
         """stda_submit: frame / out are bf16 [H][W] CUDA tensors; done an
         optional torch.cuda.Event. Returns the status (OK, WARMUP or BUSY)."""
         H, W = frame.shape[-2:]
+        if done is not None and done.cuda_event == 0:
+            # torch creates its CUDA event lazily, at the first record: create
+            # it here, or the library would receive a null event
+            done.record()
         ev = ctypes.c_void_p(done.cuda_event) if done is not None else None
         st = lib().stda_submit(self.h, radar, H, W, _ptr(frame), _ptr(out), ev, _stream(stream))
         if st not in (OK, WARMUP, ERR_BUSY):
