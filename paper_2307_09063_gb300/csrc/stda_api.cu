@@ -417,12 +417,23 @@ struct stda_ctx {
   int* d_status = nullptr;
   uint32_t wait_polls = stda::kWaitPolls;  // bound of the tensor-core kernels' tile waits
   cudaStream_t last_stream = nullptr;
-  // forward passes captured as CUDA graphs, by (input, output, B, H, W), most
-  // recent last; replayed on the caller's stream (one launch instead of seven)
+  // forward passes and training steps captured as CUDA graphs, by their
+  // buffers and shape, most recent last; replayed on the caller's stream. A
+  // call is captured the second time its key is seen (one-off calls run
+  // directly); exec is null for a key seen once.
+  struct GraphKey {
+    uintptr_t p[10];
+    int i[5];
+    bool operator==(const GraphKey& o) const {
+      for (int k = 0; k < 10; ++k)
+        if (p[k] != o.p[k]) return false;
+      for (int k = 0; k < 5; ++k)
+        if (i[k] != o.i[k]) return false;
+      return true;
+    }
+  };
   struct Graph {
-    const void* in;
-    void* out;
-    int B, H, W;
+    GraphKey key;
     int launches;
     cudaGraphExec_t exec;
   };
@@ -457,7 +468,8 @@ size_t elem_size(stda_precision p) { return p == STDA_FP32 ? 4 : 2; }
 // Captured forwards hold the weight, scratch and status pointers and the
 // wait bound as kernel parameters: drop them whenever one of those changes.
 void drop_graphs(stda_ctx* c) {
-  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
 }
 
@@ -523,6 +535,46 @@ struct Counter : stda::KernelHook {
   void end(cudaStream_t) override {}
 };
 constexpr size_t kMaxGraphs = 8;
+
+// Runs body(stream, hook) for `key`: directly the first time the key is
+// seen, then captured once as a CUDA graph on the private stream and
+// replayed on `st` (launch counts of the captured forward kernels added).
+template <typename Body>
+stda_status run_cached(stda_ctx* c, const stda_ctx::GraphKey& key, cudaStream_t st, const char* what, Body body) {
+  cudaError_t e;
+  size_t gi = 0;
+  while (gi < c->graphs.size() && !(c->graphs[gi].key == key)) ++gi;
+  if (gi == c->graphs.size()) {
+    if (c->graphs.size() == kMaxGraphs) {
+      if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({key, 0, nullptr});
+    if ((e = body(st, &c->prof))) return cuda_fail(c, e, what);
+    return STDA_OK;
+  }
+  if (!c->graphs[gi].exec) {
+    if (!c->cap && (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking))) return cuda_fail(c, e, what);
+    Counter cnt;
+    if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal))) return cuda_fail(c, e, what);
+    const cudaError_t fe = body(c->cap, &cnt);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (fe || e) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(c, fe ? fe : e, what);
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) return cuda_fail(c, e, what);
+    c->graphs[gi].exec = exec;
+    c->graphs[gi].launches = cnt.n;
+  }
+  if ((e = cudaGraphLaunch(c->graphs[gi].exec, st))) return cuda_fail(c, e, what);
+  c->prof.launches += (uint64_t)c->graphs[gi].launches;
+  return STDA_OK;
+}
 
 }  // namespace
 
@@ -688,37 +740,16 @@ stda_status stda_forward(stda_ctx* c, const void* d_in, void* d_out, int B, int 
     if (e) return cuda_fail(c, e, "forward");
     return STDA_OK;
   }
-  size_t gi = 0;
-  while (gi < c->graphs.size()) {
-    const auto& g = c->graphs[gi];
-    if (g.in == d_in && g.out == d_out && g.B == B && g.H == H && g.W == W) break;
-    ++gi;
-  }
-  if (gi == c->graphs.size()) {
-    if (!c->cap && (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking))) return cuda_fail(c, e, "forward");
-    Counter cnt;
-    if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal))) return cuda_fail(c, e, "forward");
-    const cudaError_t fe = run_forward(c, d_in, d_out, B, H, W, c->cap, &cnt);
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(c->cap, &graph);
-    if (fe || e) {
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(c, fe ? fe : e, "forward (capture)");
-    }
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e) return cuda_fail(c, e, "forward (instantiate)");
-    if (c->graphs.size() == kMaxGraphs) {
-      cudaGraphExecDestroy(c->graphs.front().exec);
-      c->graphs.erase(c->graphs.begin());
-    }
-    c->graphs.push_back({d_in, d_out, B, H, W, cnt.n, exec});
-    gi = c->graphs.size() - 1;
-  }
-  if ((e = cudaGraphLaunch(c->graphs[gi].exec, st))) return cuda_fail(c, e, "forward (graph launch)");
-  c->prof.launches += (uint64_t)c->graphs[gi].launches;
-  return STDA_OK;
+  stda_ctx::GraphKey key{};
+  key.p[0] = (uintptr_t)d_in;
+  key.p[1] = (uintptr_t)d_out;
+  key.i[0] = B;
+  key.i[1] = H;
+  key.i[2] = W;
+  key.i[3] = 1;  // forward
+  return run_cached(c, key, st, "forward", [&](cudaStream_t s, stda::KernelHook* h) {
+    return run_forward(c, d_in, d_out, B, H, W, s, h);
+  });
 }
 
 stda_status stda_forward_host(stda_ctx* c, const void* h_in, void* h_out, int B, int H, int W, cudaStream_t st) {
@@ -802,8 +833,6 @@ stda_status stda_backward_bn(stda_ctx* c, const void* d_in, const void* d_target
     if (!c->d_target32 &&
         (e = cudaMalloc((void**)&c->d_target32, sizeof(float) * c->cfg.max_batch * c->cfg.H * c->cfg.W)))
       return cuda_fail(c, e, "backward: target buffer");
-    long n = (long)B * H * W;
-    k_bf16_to_f32_flat<<<(int)((n + 255) / 256), 256, 0, st>>>((const __nv_bfloat16*)d_target, c->d_target32, n);
     target = c->d_target32;
   }
   stda::TrainArgs a{};
@@ -822,11 +851,27 @@ stda_status stda_backward_bn(stda_ctx* c, const void* d_in, const void* d_target
   a.B = B;
   a.H = H;
   a.W = W;
-  a.stream = st;
   c->last_stream = st;
   if (B == 0) return STDA_OK;
-  if ((e = stda::train_step(a, c->d_train, c->train_bytes))) return cuda_fail(c, e, "backward");
-  return STDA_OK;
+  // the step's ~270 launches (conversion of bf16 targets, taped forward,
+  // adjoint, reductions) replay as one CUDA graph from a key's second use
+  stda_ctx::GraphKey key{};
+  const void* ptrs[9] = {d_in, d_target, d_gout, d_gparams, d_loss, d_gin, d_out, d_bn_stats, c->d_train};
+  for (int k = 0; k < 9; ++k) key.p[k] = (uintptr_t)ptrs[k];
+  key.i[0] = B;
+  key.i[1] = H;
+  key.i[2] = W;
+  key.i[3] = 2 + (int)bn_mode;  // training step
+  return run_cached(c, key, st, "backward", [&](cudaStream_t s, stda::KernelHook*) {
+    if (d_target && bf) {
+      long n = (long)B * H * W;
+      k_bf16_to_f32_flat<<<(int)((n + 255) / 256), 256, 0, s>>>((const __nv_bfloat16*)d_target, c->d_target32, n);
+    }
+    stda::TrainArgs t = a;
+    t.stream = s;
+    const cudaError_t te = stda::train_step(t, c->d_train, c->train_bytes);
+    return te ? te : cudaGetLastError();
+  });
 }
 
 stda_status stda_submit(stda_ctx* c, int radar, int H, int W, const void* d_frame, void* d_out, cudaEvent_t done,
