@@ -402,9 +402,31 @@ __device__ void copy_to_smem(void* dst, const void* src, int bytes) {
   batched<8>(bytes / 16, [&](int i) { return s[i]; }, [&](int i, uint4 v) { d[i] = v; });
 }
 
-__device__ void zero_smem(void* dst, int bytes) {
-  uint4* d = (uint4*)dst;
-  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = make_uint4(0, 0, 0, 0);
+// Zeroes the plane pixels an item's valid outputs read but its staging or
+// stage 1 does not write: column zc0 and columns zc1 .. zc1 + nr - 1 (the
+// left / right zero padding; the right one includes the column that the
+// zero-weight half of a paired K-step reads) of plane rows [0, nrows), and
+// every pixel of rows [0, r_top) and [r_bot, nrows) (input rows outside the
+// map), in np planes of PIXA 16-byte pixels with row pitch WP. Everything
+// else a valid output reads is written for the item; what only discarded
+// (padding) GEMM rows read may hold the previous item's values.
+__device__ void zero_margins(unsigned char* base, int np, int PIXA, int WP, int nrows, int zc0, int zc1, int nr,
+                             int r_top, int r_bot) {
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  const int nc = 1 + nr;
+  for (int i = threadIdx.x; i < np * nrows * nc; i += blockDim.x) {
+    const int pl = i / (nrows * nc), rem = i % (nrows * nc), r = rem / nc, k = rem % nc;
+    const int c = k == 0 ? zc0 : zc1 + k - 1;
+    *(uint4*)(base + ((size_t)pl * PIXA + r * WP + c) * 16) = z;
+  }
+  r_top = max(0, min(r_top, nrows));
+  r_bot = max(r_top, min(r_bot, nrows));
+  const int nz = r_top + (nrows - r_bot);
+  for (int i = threadIdx.x; i < np * nz * WP; i += blockDim.x) {
+    const int pl = i / (nz * WP), rem = i % (nz * WP), k = rem / WP, c = rem % WP;
+    const int r = k < r_top ? k : r_bot + (k - r_top);
+    *(uint4*)(base + ((size_t)pl * PIXA + r * WP + c) * 16) = z;
+  }
 }
 
 // Waits for the MMAs, reads one accumulator row (16 columns) per call.
@@ -543,7 +565,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int oy0 = band * TY;
-  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
+  // padding of the planes: columns 0 and wo + 1, plane row 0 above the map
+  // (first band) and the rows at or below input row h
+  zero_margins(x0, 4 * G * T, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
+  zero_margins(x1, 4 * G * T, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
   eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
@@ -661,7 +686,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
           float o[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            o[j] = valid ? epi(mv[j], rv[j], M.sm[c + j], M.sr[c + j], M.b2[c + j], M.rb[c + j]) : 0.f;
+            o[j] = valid ? epi(mv[j], rv[j], F8 ? M.sm[c + j] : 1.f, F8 ? M.sr[c + j] : 1.f, M.b2[c + j], M.rb[c + j])
+                         : 0.f;
           if (valid) {
             *(uint4*)(dst + c) = f32_to_bf16x8(o);
             *(uint4*)(dst + c + 8) = f32_to_bf16x8(o + 8);
@@ -811,7 +837,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_
   for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int oy0 = band * TY, yi0 = 2 * oy0 - 3;
-  zero_smem(x0, L.planes_bytes);
+  zero_margins(x0, 4, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   // 1. this item's maps (TMA issued during the previous item)
   const bool got = mbar_wait(tbar, tpar, a.wait_polls);
@@ -878,7 +904,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_
   failed = __syncthreads_or(!ok);
   fence_after_sync();
   if (failed) break;
-  zero_smem(x1, L.planes_bytes);  // S is dead: x1 becomes the stage-1 planes
+  // S is dead: x1 becomes the stage-1 planes (their padding as for x0)
+  zero_margins(x1, 4, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
   __syncthreads();
   // 4a. stage 1 at the rows the stride-2 taps read, a pixel pair per thread
   // (as in k_enc_tc)
@@ -1032,7 +1059,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int a0 = band * TA;
-  zero_smem(sm + L.off_x0, 2 * L.planes_bytes);
+  // padding of the planes: columns 1, w + 2 and w + 3 (input columns -1, w
+  // and the column the zero half of a paired K-step reads),
+  // plane rows above the map (first band) and at or below input row h
+  zero_margins(x0, G * T, PIXA, WP, TA + 4, 1, w + 2, 2, 2 - a0, h - a0 + 2);
+  zero_margins(x1, G * T, PIXA, WP, TA + 4, 1, w + 2, 2, 2 - a0, h - a0 + 2);
   eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.red, M.g, M.sa);
   if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.red, M.g, M.ss);
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
@@ -1135,7 +1166,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
             ld_wait();
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              o[j] = valid ? epi(mv[j], rv[j], M.sm[mc + j], M.sr[mc + j], M.b2[cc + j], M.rb[cc + j]) : 0.f;
+              o[j] = valid ? epi(mv[j], rv[j], F8 ? M.sm[mc + j] : 1.f, F8 ? M.sr[mc + j] : 1.f, M.b2[cc + j],
+                                 M.rb[cc + j])
+                           : 0.f;
               sum[j] += o[j];
             }
             if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
