@@ -562,14 +562,20 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc_tc(TcArgs a) {
   bool failed = false;
 
   // persistent loop over (window, band) items
-  for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+  // a CTA takes a contiguous run of items, so consecutive items are mostly
+  // bands of one window and the window's ECA scales are reduced once
+  const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x, it_end = min(items, ((int)blockIdx.x + 1) * per);
+  int prev_b = -1;
+  for (int item = blockIdx.x * per; item < it_end && !failed; ++item) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int oy0 = band * TY;
   // padding of the planes: columns 0 and wo + 1, plane row 0 above the map
   // (first band) and the rows at or below input row h
   zero_margins(x0, 4 * G * T, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
   zero_margins(x1, 4 * G * T, PIXA, WP, TY + 2, 0, wo + 1, 1, oy0 == 0 ? 1 : 0, ho - oy0 + 1);
-  eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
+  if (b != prev_b)
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, 1.f / (float)(h * w), a.pk3, M.red, M.g, M.sa);
+  prev_b = b;
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
@@ -1056,7 +1062,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   bool failed = false;
   const float inv_n = 1.f / (float)(h * w);
 
-  for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+  // contiguous runs of items per CTA: the ECA scales of the input (and of
+  // the skip) are reduced once per window
+  const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x, it_end = min(items, ((int)blockIdx.x + 1) * per);
+  int prev_b = -1;
+  for (int item = blockIdx.x * per; item < it_end && !failed; ++item) {
   const int b = item / a.tiles_per_window, band = item % a.tiles_per_window;
   const int a0 = band * TA;
   // padding of the planes: columns 1, w + 2 and w + 3 (input columns -1, w
@@ -1064,8 +1074,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   // plane rows above the map (first band) and at or below input row h
   zero_margins(x0, G * T, PIXA, WP, TA + 4, 1, w + 2, 2, 2 - a0, h - a0 + 2);
   zero_margins(x1, G * T, PIXA, WP, TA + 4, 1, w + 2, 2, 2 - a0, h - a0 + 2);
-  eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.red, M.g, M.sa);
-  if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.red, M.g, M.ss);
+  if (b != prev_b) {
+    eca_scales(a.ppart + (size_t)b * a.ptiles * CI, a.ptiles, CI, inv_n, a.pk3, M.red, M.g, M.sa);
+    if (SKIP) eca_scales(a.spart + (size_t)b * a.stiles * CI, a.stiles, CI, inv_n, a.sk3, M.red, M.g, M.ss);
+  }
+  prev_b = b;
   for (int i = tid; i < 16 * CO; i += blockDim.x) M.red[i] = 0.f;
   __syncthreads();
 
