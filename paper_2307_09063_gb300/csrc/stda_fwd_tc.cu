@@ -969,7 +969,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  // 4b. stage 2 on the tensor cores and the epilogue (as in k_enc_tc)
+  // 4b. stage 2 on the tensor cores and the epilogue (as in k_enc_tc); each
+  // thread sums its rows' 16 channels over the tiles it drains, and the
+  // warp reduction runs once per item
+  float esum[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) esum[j] = 0.f;
   ok = run_tiles<false>(
       a, M, tmem, phases, cpt, M.dtab, a.ntile, nsteps, 2, NP, 1, 0u, 0u, [&](int i, uint32_t col, int, int) {
         int m = m_lo + 128 * i + (warp & 3) * 32 + lane;
@@ -987,8 +992,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_enc1_tc(TcArgs a, const __grid_
           *(uint4*)(dst) = f32_to_bf16x8(o);
           *(uint4*)(dst + 8) = f32_to_bf16x8(o + 8);
         }
-        warp_sums_to<16>(o, &M.red[warp * CO]);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) esum[j] += o[j];
       });
+  warp_sums_to<16>(esum, &M.red[warp * CO]);
   fence_before_sync();
   failed = __syncthreads_or(!ok);
   fence_after_sync();
@@ -1155,6 +1162,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
   __syncthreads();
   fence_after_sync();
   // stage 2 on the tensor cores and the epilogue, as in the encoder
+  // decoder 3 (8 channels): each thread sums its rows over the tiles it
+  // drains and the warp reduction runs once per item
+  float esum[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) esum[j] = 0.f;
   const int cpt = 2 * NPH * NM;  // TMEM columns per tile: (main, residual) x 4 phases
   const bool ok = run_tiles<F8>(
       a, M, tmem, phases, cpt, M.dtab, a.ntile, nsteps, 2 * NPH, NM, T, (uint32_t)(lo_off >> 4), (uint32_t)(L.wbytes / T) >> 4,
@@ -1186,9 +1198,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_dec_tc(TcArgs a) {
             }
             if (valid) *(uint4*)(dst + cc) = f32_to_bf16x8(o);
           }
-          warp_sums_to<8>(sum, &M.red[warp * CO + cc]);
+          if constexpr (CO == 8) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) esum[j] += sum[j];
+          } else {
+            warp_sums_to<8>(sum, &M.red[warp * CO + cc]);
+          }
         }
       });
+  if constexpr (CO == 8) warp_sums_to<8>(esum, &M.red[warp * CO]);
   fence_before_sync();
   failed = __syncthreads_or(!ok);
   fence_after_sync();
