@@ -399,6 +399,7 @@ struct OutArgs {
   NetW w;
   T* out;  // [B][H][W]
   const int* d_nwin;  // bf16 kernel: windows >= *d_nwin are skipped (null: all)
+  int B;              // bf16 kernel: windows in the buffers
 };
 
 constexpr int kOutTY = 16, kOutTX = 16;
@@ -634,26 +635,23 @@ cudaError_t forward_simt(const NetW& w, const T* in, T* out, int B, int H, int W
 
 // Output module for bf16 maps: the ECA weights of decoder block 3 are folded
 // into the conv weights of each window (the conv is linear in its input) and
-// kept in registers as channel pairs. A CTA takes one window and a band of
-// kOutRows output rows and streams the input rows through a shared-memory
-// ring with asynchronous copies issued kOutAhead rows ahead of use (each
-// row: W pixels x 16 bytes = 8 channels, with a zero pixel either side).
-// Each thread owns one column: input row r feeds the accumulators of output
-// rows r + 1, r and r - 1 (kernel rows 0, 1, 2); after row r, output row
-// r - 1 is complete.
-constexpr int kOutRows = 32, kOutAhead = 6, kOutRing = kOutAhead + 2;
+// kept in registers as channel pairs. Work is split by warps, not CTAs: the
+// output rows of every (window, 128-column strip) are laid end to end and
+// each warp of a persistent grid takes one contiguous run of them (balanced
+// over the windows the device-side count says are live). A warp streams the
+// input rows of its run (the run's rows +-1 at each strip change) through a
+// ring of its own in shared memory with asynchronous 16-byte copies issued
+// kOutDepth - 1 rows ahead; a row of a strip is 130 pixels (the strip and
+// one either side, zero-filled outside the map) of 16 bytes = 8 channels,
+// with a 16-byte skew after every 8 pixels so that the lanes' 16-byte reads
+// at pixels 4 l + j fall in distinct banks. Lane l computes output columns
+// 4 l .. 4 l + 3 of the strip: input row r feeds the accumulators of output
+// rows r + 1, r and r - 1 (kernel rows 0, 1, 2), after which row r - 1 is
+// complete. Only __syncwarp orders the ring; there is no CTA barrier.
+constexpr int kOutPx = 4, kOutStrip = 32 * kOutPx, kOutDepth = 6, kOutWarps = 4, kOutMinRows = 16;
+constexpr int kOutChunks = kOutStrip + 2, kOutSlot = kOutChunks + (kOutChunks + 7) / 8;
 
-__device__ __forceinline__ void out_row(const uint4 (&u)[3], const float2* wr, int dy, float2& acc) {
-#pragma unroll
-  for (int dx = 0; dx < 3; ++dx) {
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(&u[dx]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float2 f = make_float2(__uint_as_float(q[k] << 16), __uint_as_float(q[k] & 0xFFFF0000u));
-      acc = __ffma2_rn(f, wr[(dy * 3 + dx) * 4 + k], acc);
-    }
-  }
-}
+__device__ __forceinline__ int out_skew(int c) { return c + (c >> 3); }
 
 // 16-byte asynchronous global -> shared copy; zero-fills when !valid.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
@@ -667,65 +665,160 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a) {
-  extern __shared__ __align__(16) uint4 ring[];  // [kOutRing][W + 2]
-  __shared__ float s_g[64], s_s[64], s_tmp[kThreads];
-  __shared__ float s_w[72];
-  const int b = blockIdx.y, H = a.H, W = a.W, RW = W + 2;
-  if (a.d_nwin && b >= *a.d_nwin) return;
-  const int y0 = blockIdx.x * kOutRows, y1 = min(H, y0 + kOutRows);
-  const __nv_bfloat16* A = a.A + (size_t)b * H * W * 8;
-  __nv_bfloat16* out = a.out + (size_t)b * H * W;
-  // rows y0 - 1 .. y1 pass through the ring; row r sits in slot (r - y0 + 1) % kOutRing
-  auto fetch = [&](int r) {
-    if (r <= y1) {
-      uint4* dst = ring + ((r - y0 + 1) % kOutRing) * RW + 1;
-      const bool in = r >= 0 && r < H;
-      for (int x = threadIdx.x; x < W; x += blockDim.x)
-        cp_async16(dst + x, in ? (const void*)(A + ((size_t)r * W + x) * 8) : (const void*)A, in);
-    }
-    cp_async_commit();  // one group per row (empty past the band) keeps the wait count fixed
-  };
-  for (int i = threadIdx.x; i < kOutRing; i += blockDim.x) {
-    ring[i * RW] = make_uint4(0, 0, 0, 0);
-    ring[i * RW + W + 1] = make_uint4(0, 0, 0, 0);
+// A cursor over a warp's run: segment (window b, strip xs) covers map rows
+// ya .. yb - 1 of that strip and streams input rows ya - 1 .. yb (position
+// i, input row ya - 1 + i); the next segment is the next strip (the next
+// window after the last strip), from row 0, up to the end of the run (q1 in
+// the flattened (window, strip, row) order).
+struct OutCur {
+  long base;  // flattened index of row 0 of the current strip
+  int b, xs, ya, yb, i;
+  bool live;
+  __device__ void start(long q0, long q1, int H, int ns) {
+    const long k = q0 / H;
+    base = k * H;
+    b = (int)(k / ns);
+    xs = (int)(k % ns);
+    ya = (int)(q0 - base);
+    yb = (int)min(q1 - base, (long)H);
+    i = 0;
+    live = q0 < q1;
   }
-  for (int k = 0; k < kOutAhead; ++k) fetch(y0 - 1 + k);
-  eca_scales(a.Apart + (size_t)b * a.Atiles * 8, a.Atiles, 8, 1.f / (float)(H * W), a.Ak3, s_tmp, s_g, s_s);
-  for (int i = threadIdx.x; i < 72; i += blockDim.x) s_w[i] = a.w.out_w[i] * s_s[i & 7];
-  __syncthreads();
-  float2 wr[36];
-#pragma unroll
-  for (int i = 0; i < 36; ++i) wr[i] = make_float2(s_w[2 * i], s_w[2 * i + 1]);
-  const float bias = a.w.out_b[0];
-  // acc[j][0..2]: output rows r - 1, r, r + 1 of column threadIdx.x + j * blockDim.x
-  constexpr int kCols = 2;  // W <= kCols * blockDim.x
-  float2 acc[kCols][3];
-#pragma unroll
-  for (int j = 0; j < kCols; ++j)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) acc[j][q] = make_float2(0.f, 0.f);
-  for (int r = y0 - 1; r <= y1; ++r) {
-    fetch(r + kOutAhead);
-    cp_async_wait<kOutAhead>();  // row r has landed (this thread's copies)
-    __syncthreads();             // ... and every thread's
-    const uint4* row = ring + ((r - y0 + 1) % kOutRing) * RW;
-#pragma unroll
-    for (int j = 0; j < kCols; ++j) {
-      const int x = threadIdx.x + j * blockDim.x;
-      if (x >= W) break;
-      const uint4 u[3] = {row[x], row[x + 1], row[x + 2]};
-      out_row(u, wr, 2, acc[j][0]);
-      out_row(u, wr, 1, acc[j][1]);
-      out_row(u, wr, 0, acc[j][2]);
-      if (r - 1 >= y0) {
-        const float z = acc[j][0].x + acc[j][0].y + bias;
-        out[(size_t)(r - 1) * W + x] = __float2bfloat16_rn(1.f / (1.f + expf(-z)));
-      }
-      acc[j][0] = acc[j][1];
-      acc[j][1] = acc[j][2];
-      acc[j][2] = make_float2(0.f, 0.f);
+  __device__ void next(long q1, int H, int ns) {
+    if (++i < yb - ya + 2) return;
+    base += H;
+    if (++xs == ns) {
+      xs = 0;
+      ++b;
     }
+    ya = 0;
+    yb = (int)min(q1 - base, (long)H);
+    i = 0;
+    live = base < q1;
+  }
+  __device__ int row() const { return ya - 1 + i; }
+};
+
+// Chunk j of a lane (input column 4 l + j - 1 of the strip, 8 channels) into
+// the accumulators of its pixels p = j - dx (dx = 0 .. 2): acc[p][q] +=
+// the chunk times kernel row 2 - q, column dx. Each bf16 pair is unpacked
+// once for every pixel it feeds.
+template <int J>
+__device__ __forceinline__ void out_chunk(const uint4& u, const float2* wr, float2 (&acc)[kOutPx][3]) {
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = make_float2(__uint_as_float(q[k] << 16), __uint_as_float(q[k] & 0xFFFF0000u));
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const int p = J - dx;
+      if (p >= 0 && p < kOutPx) {
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) acc[p][qq] = __ffma2_rn(f, wr[((2 - qq) * 3 + dx) * 4 + k], acc[p][qq]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kOutWarps * 32) k_out_bf16(OutArgs<__nv_bfloat16> a) {
+  extern __shared__ __align__(16) uint4 ring[];  // [kOutWarps][kOutDepth][kOutSlot]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, H = a.H, W = a.W;
+  const int ns = (W + kOutStrip - 1) / kOutStrip;
+  const int nwin = a.d_nwin ? min(*a.d_nwin, a.B) : a.B;
+  const long Q = (long)nwin * ns * H, nw = (long)gridDim.x * kOutWarps;
+  const long per = max((Q + nw - 1) / nw, (long)kOutMinRows);
+  const long q0 = ((long)blockIdx.x * kOutWarps + warp) * per, q1 = min(Q, q0 + per);
+  if (q0 >= q1) return;
+  uint4* wring = ring + (size_t)warp * kOutDepth * kOutSlot;
+  const __nv_bfloat16* A = a.A;
+  OutCur fc, cc;  // fetch cursor (kOutDepth - 1 positions ahead) and compute cursor
+  fc.start(q0, q1, H, ns);
+  cc = fc;
+  int slot_f = 0;
+  auto fetch = [&]() {
+    if (fc.live) {
+      uint4* dst = wring + slot_f * kOutSlot;
+      const int r = fc.row(), x0 = fc.xs * kOutStrip - 1;
+      const bool rin = r >= 0 && r < H;
+      const __nv_bfloat16* src = A + ((size_t)fc.b * H + r) * W * 8;
+      for (int c = lane; c < kOutChunks; c += 32) {
+        const int x = x0 + c;
+        const bool in = rin && x >= 0 && x < W;
+        cp_async16(dst + out_skew(c), in ? (const void*)(src + (size_t)x * 8) : (const void*)A, in);
+      }
+      fc.next(q1, H, ns);
+    }
+    cp_async_commit();  // one group per position (empty past the run) keeps the wait count fixed
+    slot_f = slot_f + 1 == kOutDepth ? 0 : slot_f + 1;
+  };
+  for (int k = 0; k < kOutDepth - 1; ++k) fetch();
+  const float bias = a.w.out_b[0], inv_n = 1.f / (float)(H * W);
+  float2 wr[36];
+  float2 acc[kOutPx][3];  // output columns 4 l + p; [p][0]: row r - 1, [1]: r, [2]: r + 1
+  int cur_b = -1, slot = 0;
+  while (cc.live) {
+    __syncwarp();  // every lane has read the slot the next copy refills
+    fetch();
+    cp_async_wait<kOutDepth - 1>();  // this position has landed (this lane's copies)
+    __syncwarp();                    // ... and every lane's
+    const int b = cc.b, r = cc.row(), x = cc.xs * kOutStrip + kOutPx * lane;
+    if (cc.i == 0) {
+      if (b != cur_b) {
+        // ECA of the window: g = channel means from decoder block 3's band
+        // sums (fixed order), z = 1-D conv (k = 3, zero padding), s = sigmoid
+        float g = 0.f;
+        if (lane < 8) {
+          const float* part = a.Apart + (size_t)b * a.Atiles * 8;
+          for (int t = 0; t < a.Atiles; ++t) g += part[t * 8 + lane];
+          g *= inv_n;
+        }
+        const float gm = __shfl_up_sync(0xffffffffu, g, 1), gp = __shfl_down_sync(0xffffffffu, g, 1);
+        float z = a.Ak3[1] * g;
+        if (lane > 0) z += a.Ak3[0] * gm;
+        if (lane < 7) z += a.Ak3[2] * gp;
+        const float sg = 1.f / (1.f + expf(-z));
+        float sc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sc[c] = __shfl_sync(0xffffffffu, sg, c);
+#pragma unroll
+        for (int i = 0; i < 36; ++i)
+          wr[i] = make_float2(a.w.out_w[2 * i] * sc[(2 * i) & 7], a.w.out_w[2 * i + 1] * sc[(2 * i + 1) & 7]);
+        cur_b = b;
+      }
+#pragma unroll
+      for (int p = 0; p < kOutPx; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[p][q] = make_float2(0.f, 0.f);
+    }
+    const uint4* row = wring + slot * kOutSlot;
+#pragma unroll
+    for (int j = 0; j < kOutPx + 2; ++j) {
+      const uint4 u = row[out_skew(kOutPx * lane + j)];
+      switch (j) {
+        case 0: out_chunk<0>(u, wr, acc); break;
+        case 1: out_chunk<1>(u, wr, acc); break;
+        case 2: out_chunk<2>(u, wr, acc); break;
+        case 3: out_chunk<3>(u, wr, acc); break;
+        case 4: out_chunk<4>(u, wr, acc); break;
+        default: out_chunk<5>(u, wr, acc); break;
+      }
+    }
+    if (cc.i >= 2 && x < W) {
+      float o[kOutPx];
+#pragma unroll
+      for (int p = 0; p < kOutPx; ++p) o[p] = __fdividef(1.f, 1.f + __expf(-(acc[p][0].x + acc[p][0].y + bias)));
+      const __nv_bfloat162 o01 = __floats2bfloat162_rn(o[0], o[1]), o23 = __floats2bfloat162_rn(o[2], o[3]);
+      *(uint2*)(a.out + ((size_t)b * H + r - 1) * W + x) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&o01), *reinterpret_cast<const uint32_t*>(&o23));
+    }
+#pragma unroll
+    for (int p = 0; p < kOutPx; ++p) {
+      acc[p][0] = acc[p][1];
+      acc[p][1] = acc[p][2];
+      acc[p][2] = make_float2(0.f, 0.f);
+    }
+    cc.next(q1, H, ns);
+    slot = slot + 1 == kOutDepth ? 0 : slot + 1;
   }
   cp_async_wait<0>();
 }
@@ -733,13 +826,20 @@ __global__ void __launch_bounds__(kThreads) k_out_bf16(OutArgs<__nv_bfloat16> a)
 cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float* part5, int tiles5,
                             __nv_bfloat16* out, int B, int H, int W, cudaStream_t st, KernelHook* hook,
                             const int* d_nwin) {
-  OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out, d_nwin};
-  const int threads = std::min(kThreads, (W + 31) / 32 * 32);
-  if (W > 2 * threads) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)kOutRing * (W + 2) * 16;
+  if (W % kOutPx) return cudaErrorInvalidValue;
+  OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out, d_nwin, B};
+  constexpr size_t smem = (size_t)kOutWarps * kOutDepth * kOutSlot * 16;
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_out_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_out_bf16, kOutWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const long rows = (long)B * ((W + kOutStrip - 1) / kOutStrip) * H;
+  const int grid = (int)std::max<long>(1, std::min<long>((long)simt_sm_count() * per_sm,
+                                                          (rows + kOutMinRows * kOutWarps - 1) / (kOutMinRows * kOutWarps)));
   hook->begin(K_OUT, st);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_out_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_out_bf16<<<dim3(cdiv(H, kOutRows), B), threads, smem, st>>>(a);
+  k_out_bf16<<<grid, kOutWarps * 32, smem, st>>>(a);
   hook->end(st);
   return cudaGetLastError();
 }
