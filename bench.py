@@ -595,9 +595,10 @@ def main():
 
     # end to end through the public API on host buffers (stda_forward_host):
     # every step copies its pinned host input to the device, denoises it and
-    # copies the output back; a step's input copy overlaps the previous
-    # step's kernels, so the K steps are timed as one region (events on the
-    # launching stream around all of them, every copy inside it)
+    # delivers the output to pinned host memory (the output kernel stores it
+    # there directly); a step's input copy overlaps the previous step's
+    # kernels, so the K steps are timed as one region (events on the
+    # launching stream around all of them, every transfer inside it)
     xh = x.cpu().pin_memory()
     oh = torch.empty((B, 1, H, W), dtype=dtype).pin_memory()
     for _ in range(2):  # allocates the two staging pairs (and captures each one's forward)
@@ -640,7 +641,7 @@ def main():
             "step_roofline": main_res["step_roofline"],
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * esz),
                     "d2h_bytes_per_step": int(oh.numel() * esz),
-                    "call": "stda_forward_host on pinned host buffers; each step's input copy overlaps the previous step's kernels; L2 flush inside the region"},
+                    "call": "stda_forward_host on pinned host buffers; each step's input copy overlaps the previous step's kernels; the output kernel stores the result straight into the pinned host output; L2 flush inside the region"},
             "clocks": main_res["clocks"], "gpu_launches": main_res["gpu_launches"]}
     if configs:
         line["configs"] = configs

@@ -176,8 +176,12 @@ stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
  * staging buffers on an internal stream that waits only for the forward that
  * last read that buffer (two calls back), so a call's input copy overlaps the
  * previous call's kernels; the forward runs on `stream` once its input has
- * landed, and the output is copied back on a second internal stream, which
- * `stream` then waits for. So: h_in must hold its final contents when the
+ * landed. Where h_out is page-locked and mapped into the device's address
+ * space (cudaHostAlloc / cudaHostRegister memory, e.g. a pinned torch
+ * tensor) and 16-byte aligned, the forward's last kernel stores the result
+ * straight into it (NVLink-C2C on Grace-Blackwell, no copy back);
+ * otherwise the output is copied back from a staging buffer on a second
+ * internal stream, which `stream` then waits for. So: h_in must hold its final contents when the
  * call is made (it is not ordered after work already queued on `stream`);
  * h_out is complete once `stream` has been synchronised; work queued on
  * `stream` after the call follows the copy back. Calls on one context must

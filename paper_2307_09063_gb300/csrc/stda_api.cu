@@ -782,10 +782,22 @@ stda_status stda_forward_host(stda_ctx* c, const void* h_in, void* h_out, int B,
   if ((e = cudaMemcpyAsync(c->d_hin[k], h_in, nin, cudaMemcpyHostToDevice, c->h2d)) ||
       (e = cudaEventRecord(c->ev_h[k], c->h2d)) || (e = cudaStreamWaitEvent(st, c->ev_h[k], 0)))
     return cuda_fail(c, e, "forward_host: input copy");
-  const stda_status r = stda_forward(c, c->d_hin[k], c->d_hout[k], B, H, W, st);
+  // page-locked, device-mapped h_out (16-byte aligned): the output kernel
+  // stores the result straight into it over the host link, so no copy back
+  // is queued and the next call's forward need not wait for one
+  void* direct = nullptr;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, h_out) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer && ((uintptr_t)pa.devicePointer & 15) == 0)
+      direct = pa.devicePointer;
+  } else {
+    cudaGetLastError();  // an unknown pointer is not an error here: the staged copy serves it
+  }
+  const stda_status r = stda_forward(c, c->d_hin[k], direct ? direct : c->d_hout[k], B, H, W, st);
   if (r != STDA_OK) return r;
   if ((e = cudaEventRecord(c->ev_f[k], st))) return cuda_fail(c, e, "forward_host");
   c->f_recorded[k] = true;
+  if (direct) return STDA_OK;
   if ((e = cudaStreamWaitEvent(c->d2h, c->ev_f[k], 0)) ||
       (e = cudaMemcpyAsync(h_out, c->d_hout[k], nout, cudaMemcpyDeviceToHost, c->d2h)) ||
       (e = cudaEventRecord(c->ev_d[k], c->d2h)) || (e = cudaStreamWaitEvent(st, c->ev_d[k], 0)))

@@ -1,7 +1,8 @@
 """stda_forward_host: the forward pass on host buffers (input copied in on
 an internal stream into one of two staging buffers, forward on the caller's
-stream, output copied back) gives exactly the device-buffer forward's result,
-for back-to-back calls that overlap, pinned or pageable memory."""
+stream, output stored straight into page-locked host memory or copied back
+from a staging buffer) gives exactly the device-buffer forward's result, for
+back-to-back calls that overlap, pinned or pageable memory."""
 import pytest
 import torch
 
@@ -49,6 +50,32 @@ def test_host_forward_back_to_back_calls(stda):
         ctx.forward_host(x.pin_memory(), o)
     torch.cuda.synchronize()
     assert torch.equal(o, refs[2])
+
+
+def test_host_forward_direct_and_staged_outputs(stda):
+    """A 16-byte aligned pinned output is written by the output kernel itself;
+    a pinned output at an 8-byte offset and a pageable one go through the
+    staging buffer and the copy back. All three equal the device forward,
+    also when the calls alternate without synchronising."""
+    B, H, W = 3, 64, 64
+    ctx = stda.Context(H, W, B, "bf16", 0)
+    g = torch.Generator(device="cpu").manual_seed(14)
+    xs = [torch.rand((B, 3, H, W), generator=g).to(torch.bfloat16) for _ in range(3)]
+    refs = [ctx.forward(x.cuda()).cpu() for x in xs]
+    torch.cuda.synchronize()
+    n = B * H * W
+    aligned = torch.empty((B, 1, H, W), dtype=torch.bfloat16).pin_memory()
+    buf = torch.empty(n + 8, dtype=torch.bfloat16).pin_memory()
+    offset = buf[4:4 + n].view(B, 1, H, W)
+    assert aligned.data_ptr() % 16 == 0 and offset.data_ptr() % 16 == 8
+    pageable = torch.empty((B, 1, H, W), dtype=torch.bfloat16)
+    outs = (aligned, offset, pageable)
+    for _ in range(2):
+        for x, o in zip(xs, outs):
+            ctx.forward_host(x.pin_memory(), o)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
 
 
 def test_host_forward_pageable_and_smaller_batch(stda):
