@@ -482,7 +482,8 @@ __global__ void __launch_bounds__(256) k_wgrad_s1(const float* __restrict__ A, c
 // used; the weights come re-laid as wT[m][ky kx][n] (k_wt), 16 bytes a copy,
 // as do the transposed form's source rows. 256 threads: warp w = (row group or output phase, channel group);
 // lane = (row in the warp, column), TX columns per warp row. Sums run in FP32
-// over m, then ky, kx.
+// over m, then ky, kx; a thread's output channels 2 j and 2 j + 1 share one
+// packed FMA (fma.rn.f32x2: two IEEE FMAs, the same results).
 constexpr int kDcMC = 4;  // source channels per stage
 constexpr long kDcWT = 32768;  // largest dense conv weight tensor (64 x 32 x 4 x 4)
 
@@ -562,11 +563,11 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
     }
     cp_async_commit();
   };
-  float acc[NP][NO];
+  float2 acc[NP][NO / 2];
 #pragma unroll
   for (int i = 0; i < NP; ++i)
 #pragma unroll
-    for (int j = 0; j < NO; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < NO / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
   issue(0, dsm);
   int stage = 0;
   for (int m0 = 0; m0 < M; m0 += kDcMC, ++stage) {
@@ -592,7 +593,8 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
           for (int i = 0; i < NP; ++i) {
             const float xv = xb[m * CS + (2 * i * RW + ky) * RS + (kx & 1) * PW + (kx >> 1)];
 #pragma unroll
-            for (int j = 0; j < NO; ++j) acc[i][j] += xv * wv[j];
+            for (int j = 0; j < NO / 2; ++j)  // output channels 2 j, 2 j + 1: two FMAs in one instruction
+              acc[i][j] = __ffma2_rn(make_float2(xv, xv), make_float2(wv[2 * j], wv[2 * j + 1]), acc[i][j]);
           }
         }
     }
@@ -608,7 +610,8 @@ __global__ void __launch_bounds__(256) k_sconv(const float* __restrict__ src, co
       const int n = n0 + cg * NO + j;
       if (n >= N) continue;
       float* o = out + ((size_t)b * N + n) * oplane + (size_t)Y * Wo + X;
-      *o = accumulate ? *o + acc[i][j] : acc[i][j] + (bias ? bias[n] : 0.f);
+      const float v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+      *o = accumulate ? *o + v : v + (bias ? bias[n] : 0.f);
     }
   }
 }
@@ -625,7 +628,7 @@ struct StconvGeo {
 // the taps of output phase (PY, PX) of k_stconv: ky = ky0 + 2 sy < K with
 // ky0 = (PY + 1) mod 2, source row offset (PY + 1 - ky) / 2 (likewise x)
 template <int K, int NO, int TX, int NP, int PY, int PX>
-__device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, float (&acc)[NP][NO]) {
+__device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, float2 (&acc)[NP][NO / 2]) {
   using G = StconvGeo<K, NO, TX, NP>;
   constexpr int KY0 = (PY + 1) & 1, KX0 = (PX + 1) & 1;
   constexpr int NTY = KY0 + 2 < K ? 2 : 1, NTX = KX0 + 2 < K ? 2 : 1;
@@ -643,7 +646,8 @@ __device__ __forceinline__ void stconv_phase(const float* xb, const float* wb, f
         for (int i = 0; i < G::NP; ++i) {
           const float xv = xb[m * G::CS + (i * G::RW + 1 + dy) * G::RS + 1 + dx];
 #pragma unroll
-          for (int j = 0; j < NO; ++j) acc[i][j] += xv * wv[j];
+          for (int j = 0; j < NO / 2; ++j)  // output channels 2 j, 2 j + 1: two FMAs in one instruction
+            acc[i][j] = __ffma2_rn(make_float2(xv, xv), make_float2(wv[2 * j], wv[2 * j + 1]), acc[i][j]);
         }
       }
 }
@@ -682,11 +686,11 @@ __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, c
     }
     cp_async_commit();
   };
-  float acc[NP][NO];
+  float2 acc[NP][NO / 2];
 #pragma unroll
   for (int i = 0; i < NP; ++i)
 #pragma unroll
-    for (int j = 0; j < NO; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < NO / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
   issue(0, dsm);
   int stage = 0;
   for (int m0 = 0; m0 < M; m0 += kDcMC, ++stage) {
@@ -719,7 +723,8 @@ __global__ void __launch_bounds__(256) k_stconv(const float* __restrict__ src, c
       const int n = n0 + cg * NO + j;
       if (n >= N) continue;
       float* o = out + ((size_t)b * N + n) * oplane + (size_t)Y * Wo + X;
-      *o = accumulate ? *o + acc[i][j] : acc[i][j] + (bias ? bias[n] : 0.f);
+      const float v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+      *o = accumulate ? *o + v : v + (bias ? bias[n] : 0.f);
     }
   }
 }
