@@ -177,14 +177,15 @@ stda_status stda_forward(stda_ctx* ctx, const void* d_in, void* d_out, int B,
  * last read that buffer (two calls back), so a call's input copy overlaps the
  * previous call's kernels; the forward runs on `stream` once its input has
  * landed. Where h_out is page-locked and mapped into the device's address
- * space (cudaHostAlloc / cudaHostRegister memory, e.g. a pinned torch
- * tensor) and 16-byte aligned, the forward's last kernel stores the result
- * straight into it (NVLink-C2C on Grace-Blackwell, no copy back);
- * otherwise the output is copied back from a staging buffer on a second
- * internal stream, which `stream` then waits for. So: h_in must hold its final contents when the
- * call is made (it is not ordered after work already queued on `stream`);
- * h_out is complete once `stream` has been synchronised; work queued on
- * `stream` after the call follows the copy back. Calls on one context must
+ * space (cudaHostAlloc / cudaHostRegister memory with the context's device
+ * current, e.g. a pinned torch tensor) and 16-byte aligned, the forward's
+ * last kernel stores the result straight into it (NVLink-C2C on
+ * Grace-Blackwell, no copy back); otherwise the output is copied back from
+ * a staging buffer on a second internal stream, which `stream` then waits
+ * for. So: h_in must hold its final contents when the call is made (it is
+ * not ordered after work already queued on `stream`); h_out is complete
+ * once `stream` has been synchronised; work queued on `stream` after the
+ * call follows the output. Calls on one context must
  * use one stream. The first call allocates the staging buffers (two pairs of
  * max_batch windows of the context's H x W). Shapes as for stda_forward. */
 stda_status stda_forward_host(stda_ctx* ctx, const void* h_in, void* h_out, int B,

@@ -782,13 +782,16 @@ stda_status stda_forward_host(stda_ctx* c, const void* h_in, void* h_out, int B,
   if ((e = cudaMemcpyAsync(c->d_hin[k], h_in, nin, cudaMemcpyHostToDevice, c->h2d)) ||
       (e = cudaEventRecord(c->ev_h[k], c->h2d)) || (e = cudaStreamWaitEvent(st, c->ev_h[k], 0)))
     return cuda_fail(c, e, "forward_host: input copy");
-  // page-locked, device-mapped h_out (16-byte aligned): the output kernel
-  // stores the result straight into it over the host link, so no copy back
-  // is queued and the next call's forward need not wait for one
+  // page-locked, device-mapped h_out (16-byte aligned, allocated or
+  // registered with this device current): the output kernel stores the
+  // result straight into it over the host link, so no copy back is queued
+  // and the next call's forward need not wait for one
   void* direct = nullptr;
   cudaPointerAttributes pa{};
-  if (cudaPointerGetAttributes(&pa, h_out) == cudaSuccess) {
-    if (pa.type == cudaMemoryTypeHost && pa.devicePointer && ((uintptr_t)pa.devicePointer & 15) == 0)
+  int dev = -1;
+  if (cudaPointerGetAttributes(&pa, h_out) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.device == dev && pa.devicePointer &&
+        ((uintptr_t)pa.devicePointer & 15) == 0)
       direct = pa.devicePointer;
   } else {
     cudaGetLastError();  // an unknown pointer is not an error here: the staged copy serves it
