@@ -829,9 +829,13 @@ cudaError_t launch_out_bf16(const NetW& w, const __nv_bfloat16* d3, const float*
   if (W % kOutPx) return cudaErrorInvalidValue;
   OutArgs<__nv_bfloat16> a{d3, part5, w.blk[5].eca, tiles5, H, W, w, out, d_nwin, B};
   constexpr size_t smem = (size_t)kOutWarps * kOutDepth * kOutSlot * 16;
+  // the attribute is per device: set it at every launch (a host-side call)
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_out_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+  }
   static int per_sm = 0;
   if (!per_sm) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_out_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_out_bf16, kOutWarps * 32, smem);
     if (per_sm < 1) per_sm = 1;
   }
