@@ -19,7 +19,7 @@ def stda():
     return S
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "fp32"])
 def test_host_forward_equals_device_forward(stda, prec):
     B, H, W = 7, 64, 96
     ctx = stda.Context(H, W, B, prec, 0)
